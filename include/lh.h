@@ -1,0 +1,207 @@
+/*
+ * lh.h -- C ABI of liblh.so, a single-GPU (NVIDIA B300, sm_103a) implementation of
+ * the matrix-free, partially assembled, sum-factorized Lagrange-phase hot path of
+ * high-order finite-element Lagrangian hydrodynamics (arXiv 2112.07075).
+ *
+ * Method (paper Section 3.3, Eqs. 14-18, single material):
+ *     M_v dv/dt = -F.1,   rho|J| = rho0|J0|,   M_E de/dt = F^T v,   dx/dt = v,
+ * with every operator applied through the decomposition A = G^T B^T D B G of
+ * Section 3.1 (the parallel P/P^T factor is the identity on one GPU) and the
+ * tensor-product sum factorization of Section 3.2.
+ *
+ * Spaces: continuous H1 velocity/position space Q_p on GLL nodes, discontinuous
+ * L2 energy space Q_{p-1} on Gauss-Legendre nodes, Gauss-Legendre quadrature with
+ * q1 points per direction, structured nx x ny (x nz) quad/hex mesh of a box whose
+ * vertices the caller supplies (they may be jittered inside the box).
+ *
+ * Data layout (all FP64, little endian):
+ *   H1 vector fields x, v, accelerations, F.1 : [dim][N_H1], component-major;
+ *       node g = gx + N1x*(gy + N1y*gz), N1x = nx*p + 1 (likewise y, z).
+ *   L2 fields e, F^T v                        : [NE][p^dim]; element
+ *       e = ex + nx*(ey + ny*ez), local node jx + p*(jy + p*jz).
+ *   Force quadrature data (lh_copy_qdata)     : [NE][dim*dim][q1^dim], entry
+ *       (c, l) = omega detJ (sigma J^{-T})_{c l}, qpoint kx + q1*(ky + q1*kz).
+ *
+ * Ownership: state buffers (x, v, e, right-hand sides, outputs) are caller-owned
+ * DEVICE memory. The context owns every other device buffer; all of them are
+ * allocated once in lh_setup (one arena) and freed in lh_destroy. No entry point
+ * allocates device memory after setup.
+ *
+ * Streams: every compute call is asynchronous on the given stream (0 = legacy
+ * default stream) and returns after enqueueing. Scalar results (time-step
+ * estimate, solver info) are written to caller-provided DEVICE memory.
+ *
+ * Errors: every call returns an lh_status. Argument errors are detected on the
+ * host before anything is enqueued. Conditions found on the device (inverted
+ * element, CG not converged, bounded wait expired) are written to the status
+ * field of the info struct of the call that found them and are also latched in
+ * the context; lh_sync_status() waits for the context's work and returns (and
+ * clears) the latched device status. lh_last_error() describes the last error.
+ *
+ * Threading: a context must not be used from two host threads at once, and
+ * calls on one context that overlap on the GPU (different streams without
+ * ordering) race on the context's internal buffers.
+ */
+#ifndef LH_H
+#define LH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lh_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  LH_OK = 0,
+  LH_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad option) */
+  LH_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  LH_ERR_OOM = 3,           /* the setup arena could not be allocated */
+  LH_ERR_INVERTED = 4,      /* det J <= 0 at some quadrature point */
+  LH_ERR_NOT_CONVERGED = 5, /* CG reached max_it before the tolerance */
+  LH_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
+  LH_ERR_UNSUPPORTED = 7    /* (dim, order, q1) combination not compiled */
+} lh_status;
+
+typedef enum { LH_PROBLEM_TAYLOR_GREEN = 0, LH_PROBLEM_GRESHO = 1 } lh_problem;
+typedef enum { LH_SOURCE_NONE = 0, LH_SOURCE_TAYLOR_GREEN_2D = 1 } lh_source;
+typedef enum { LH_PRECISION_FP64 = 0, LH_PRECISION_FP32_IR = 1 } lh_precision;
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int nx, ny, nz;           /* elements per direction (nz ignored for dim 2) */
+  const double *vertices;   /* HOST, [(nx+1)(ny+1)(nz+1)][dim], vertex vx + (nx+1)(vy + (ny+1) vz);
+                               copied during lh_setup, may be freed afterwards */
+  int order;                /* H1 order p in 1..4; L2 order is p-1 */
+  int q1;                   /* Gauss-Legendre points per direction */
+  double gamma;             /* ideal-gas exponent (> 1) */
+  double cfl;               /* CFL number of the time-step estimate (> 0) */
+  int use_viscosity;        /* 1: tensor artificial viscosity on, 0: off */
+  int source;               /* lh_source */
+  int precision;            /* lh_precision used by lh_rk2avg_step's mass solves */
+} lh_params;
+
+/* Sizes of a context's spaces. */
+typedef struct {
+  int64_t ne;      /* elements */
+  int64_t n_h1;    /* scalar H1 nodes */
+  int64_t nv;      /* vector H1 DOFs = dim * n_h1 */
+  int64_t n_l2;    /* L2 DOFs = ne * p^dim */
+  int64_t nq;      /* quadrature points = ne * q1^dim */
+  int64_t arena_bytes; /* device bytes owned by the context */
+} lh_sizes;
+
+/* Result of one mass solve; lives in DEVICE memory. */
+typedef struct {
+  int iters;        /* CG iterations taken */
+  int status;       /* LH_OK or LH_ERR_NOT_CONVERGED / LH_ERR_TIMEOUT */
+  double rel_res;   /* final ||r||_2 / ||b||_2 (0 when b = 0) */
+  double b_norm;    /* ||b||_2 over free DOFs */
+} lh_cg_info;
+
+/* Running time-integration record; lives in DEVICE memory. The caller sets t and
+   t_end before the first step (e.g. by cudaMemcpy); lh_rk2avg_step updates it. */
+typedef struct {
+  double t;           /* current time, advanced by dt each step */
+  double t_end;       /* final time used to cap a CFL-controlled step */
+  double dt;          /* step size used by the last step */
+  double dt_est;      /* CFL time-step estimate from the last step's stage 1 */
+  double energy_src;  /* dt * sum_j b_j of the last step (energy added by the source) */
+  double cg_rel_res[2];
+  int cg_iters[2];    /* CG iterations of the last step's two mass solves */
+  int status;         /* LH_OK or the first device-side error of the last step */
+  int steps;          /* steps taken with this record */
+} lh_step_info;
+
+typedef struct lh_ctx lh_ctx;
+
+/* Set up a context: copies the vertices, builds the H1 node positions x0
+ * (multilinear vertex map at the GLL nodes), the basis tables, the mass
+ * quadrature data omega*rho0*detJ0 (Section 3.2), the initial inverse
+ * Jacobians, the element energy-mass inverses M_E^{-1} (Eq. 17), the Jacobi
+ * diagonal of M_v, and allocates the arena. rho0_q: optional DEVICE array
+ * [NE][q1^dim] of initial densities at quadrature points (NULL: rho0 = 1).
+ * Returns LH_ERR_INVERTED if det J0 <= 0 anywhere, LH_ERR_UNSUPPORTED if the
+ * (dim, order, q1) kernels are not compiled in. Synchronous. */
+lh_status lh_setup(const lh_params *params, const double *rho0_q, lh_ctx **out);
+
+/* Release every resource of the context (NULL is accepted). Synchronous. */
+void lh_destroy(lh_ctx *ctx);
+
+/* Sizes of the context's spaces. */
+lh_status lh_get_sizes(const lh_ctx *ctx, lh_sizes *out);
+
+/* Message of the last error on this context (or of the last failed lh_setup when
+ * ctx is NULL). Never NULL. */
+const char *lh_last_error(const lh_ctx *ctx);
+
+/* Wait for all work enqueued by the context and return the first device-side
+ * error latched since the last call (then clear it), or LH_ERR_CUDA. */
+lh_status lh_sync_status(lh_ctx *ctx);
+
+/* Initial state of an analytic problem: x = x0 (H1 node positions), v = nodal
+ * interpolation of the problem's velocity (zero on constrained DOFs), e = the
+ * element-local L2 projection of p0 / ((gamma - 1) rho0) (Section 3.3 spaces).
+ * x, v: DEVICE [dim][N_H1]; e: DEVICE [NE][p^dim]. */
+lh_status lh_init_state(lh_ctx *ctx, int problem, double *x, double *v, double *e,
+                        lh_stream_t stream);
+
+/* Quadrature-point data update (Section 6, "quadrature point data" and
+ * "artificial viscosity"; Eqs. 1-5 stress, Eq. 16 density): from the state
+ * (x, v: DEVICE [dim][N_H1]; e: DEVICE [NE][p^dim]) computes, per quadrature
+ * point, the Jacobian, its determinant and inverse, rho = rho0 detJ0 / detJ,
+ * ideal-gas pressure and sound speed, tensor artificial viscosity, the stress
+ * sigma and the force data omega detJ sigma J^{-T}, stored in the context for
+ * the following force products. If dt_est is not NULL, also writes the CFL
+ * time-step estimate (one DEVICE double; 0 if an element is inverted). */
+lh_status lh_update_qdata(lh_ctx *ctx, const double *x, const double *v, const double *e,
+                          double *dt_est, lh_stream_t stream);
+
+/* Copy the force quadrature data of the last lh_update_qdata into out (DEVICE,
+ * [NE][dim*dim][q1^dim]). */
+lh_status lh_copy_qdata(lh_ctx *ctx, double *out, lh_stream_t stream);
+
+/* Force product (Eq. 14 right-hand side): rhs = F u, where
+ * F_{(i,c),j} = sum_q phi_j(q) sum_l dw_i/dxi_l(q) D_q[c,l] with the force data
+ * of the last lh_update_qdata. u: DEVICE [NE][p^dim] or NULL for u = 1 (F.1).
+ * rhs: DEVICE [dim][N_H1], overwritten; no boundary conditions applied. */
+lh_status lh_force_mult(lh_ctx *ctx, const double *u, double *rhs, lh_stream_t stream);
+
+/* Transposed force product (Eq. 17 right-hand side): out = F^T v.
+ * v: DEVICE [dim][N_H1]; out: DEVICE [NE][p^dim], overwritten. */
+lh_status lh_force_mult_t(lh_ctx *ctx, const double *v, double *out, lh_stream_t stream);
+
+/* Mass product (Section 3.2, y = B^T D B x per element, then G^T):
+ * y = M_v x with M_v = I_dim (x) M, M_ij = sum_q omega rho0 detJ0 w_i w_j.
+ * x, y: DEVICE [dim][N_H1] (must not alias); no boundary conditions applied. */
+lh_status lh_mass_mult(lh_ctx *ctx, const double *x, double *y, lh_stream_t stream);
+
+/* Velocity mass solve (Eq. 14, "inversion of a global CG mass matrix", Section 6):
+ * Jacobi-preconditioned CG for M_v x = b on the free DOFs (v.n = 0 on the box
+ * faces; x is set to 0 on constrained DOFs and b is ignored there), stopping when
+ * ||r||_2 <= rel_tol ||b||_2 or after max_it iterations. x: in = initial guess,
+ * out = solution. b, x: DEVICE [dim][N_H1]. info: DEVICE lh_cg_info or NULL.
+ * One persistent cooperative launch; convergence is decided on the device. */
+lh_status lh_mass_cg(lh_ctx *ctx, const double *b, double *x, double rel_tol, int max_it,
+                     lh_cg_info *info, lh_stream_t stream);
+
+/* Energy solve (Eq. 17): out = M_E^{-1} rhs element by element with the dense
+ * inverses built at setup. rhs, out: DEVICE [NE][p^dim] (must not alias). */
+lh_status lh_energy_solve(lh_ctx *ctx, const double *rhs, double *out, lh_stream_t stream);
+
+/* One RK2-average step of Eqs. 14-18 (two stages; the force data of a stage is
+ * computed once and used for both F.1 and F^T v, which conserves total energy
+ * up to the solver tolerance). x, v, e: DEVICE state, updated in place.
+ * dt > 0: fixed step. dt <= 0: dt = min(dt_est(stage 1), info->t_end - info->t).
+ * info: DEVICE lh_step_info (required; t and t_end must be initialised).
+ * Mass solves: Jacobi-PCG to rel_tol (<= 0: 1e-12), max_it (<= 0: 1000),
+ * warm-started from the previous solve's acceleration. */
+lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt,
+                         double rel_tol, int max_it, lh_step_info *info, lh_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LH_H */
