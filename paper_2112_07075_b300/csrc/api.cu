@@ -1,0 +1,591 @@
+// Host implementation of the C ABI declared in include/lh.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lh_device.cuh"
+#include "lh_internal.h"
+
+using namespace lh;
+
+namespace {
+
+constexpr int kNodeThreads = 256;
+
+struct Zs { double z[5]; };
+
+// ---------------------------------------------------------------------------
+// Node-wise kernels (one thread per H1 DOF or L2 DOF).
+// ---------------------------------------------------------------------------
+
+// H1 node positions: multilinear map of the owning (lowest-index) element at the GLL nodes.
+__global__ void k_nodes_x0(MeshDesc m, int dim, int p, Zs z, const double *__restrict__ V, double *__restrict__ x0) {
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)m.nh1;
+       g += (size_t)gridDim.x * blockDim.x) {
+    int gc[3] = {(int)(g % m.n1x), (int)((g / m.n1x) % m.n1y), dim == 3 ? (int)(g / ((size_t)m.n1x * m.n1y)) : 0};
+    const int nel[3] = {m.nx, m.ny, m.nz};
+    int ec[3];
+    double xi[3];
+    for (int a = 0; a < dim; ++a) {
+      ec[a] = min(gc[a] / p, nel[a] - 1);
+      xi[a] = z.z[gc[a] - ec[a] * p];
+    }
+    double X[3] = {0.0, 0.0, 0.0};
+    const int ncorner = 1 << dim;
+    for (int k = 0; k < ncorner; ++k) {
+      double w = 1.0;
+      size_t vi = 0, stride = 1;
+      for (int a = 0; a < dim; ++a) {
+        const int c = (k >> a) & 1;
+        w *= c ? xi[a] : 1.0 - xi[a];
+        vi += (size_t)(ec[a] + c) * stride;
+        stride *= (size_t)(nel[a] + 1);
+      }
+      for (int a = 0; a < dim; ++a) X[a] += w * V[vi * dim + a];
+    }
+    for (int a = 0; a < dim; ++a) x0[(size_t)a * m.nh1 + g] = X[a];
+  }
+}
+
+__device__ __forceinline__ bool constrained(const MeshDesc &m, int dim, size_t g, int c) {
+  size_t gc;
+  int n1;
+  if (c == 0) { gc = g % m.n1x; n1 = m.n1x; }
+  else if (c == 1) { gc = (g / m.n1x) % m.n1y; n1 = m.n1y; }
+  else { gc = g / ((size_t)m.n1x * m.n1y); n1 = m.n1z; }
+  (void)dim;
+  return gc == 0 || gc == (size_t)(n1 - 1);
+}
+
+// invdiag[c][g] = 0 on constrained DOFs, 1/diag(M)[g] elsewhere.
+__global__ void k_invdiag(MeshDesc m, int dim, const double *__restrict__ diag, double *__restrict__ invdiag) {
+  const size_t n = (size_t)dim * m.nh1;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k / m.nh1);
+    const size_t g = k % m.nh1;
+    invdiag[k] = constrained(m, dim, g, c) ? 0.0 : 1.0 / diag[g];
+  }
+}
+
+// Initial velocity: nodal interpolation of the problem's analytic velocity, 0 on constrained DOFs.
+__global__ void k_init_v(MeshDesc m, int dim, int problem, const double *__restrict__ x0, double *__restrict__ x,
+                         double *__restrict__ v) {
+  const double pi = 3.141592653589793;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (size_t)m.nh1;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const double X = x0[g], Y = x0[m.nh1 + g], Z = dim == 3 ? x0[2 * (size_t)m.nh1 + g] : 0.0;
+    double vv[3] = {0.0, 0.0, 0.0};
+    if (problem == LH_PROBLEM_TAYLOR_GREEN) {
+      if (dim == 2) {
+        vv[0] = sin(pi * X) * cos(pi * Y);
+        vv[1] = -cos(pi * X) * sin(pi * Y);
+      } else {
+        vv[0] = sin(pi * X) * cos(pi * Y) * cos(pi * Z);
+        vv[1] = -cos(pi * X) * sin(pi * Y) * cos(pi * Z);
+        vv[2] = 0.0;
+      }
+    } else {
+      const double r = sqrt(X * X + Y * Y);
+      const double vt = r < 0.2 ? 5.0 * r : (r < 0.4 ? 2.0 - 5.0 * r : 0.0);
+      const double rs = r > 0.0 ? r : 1.0;
+      vv[0] = -vt * Y / rs;
+      vv[1] = vt * X / rs;
+    }
+    for (int c = 0; c < dim; ++c) {
+      const size_t k = (size_t)c * m.nh1 + g;
+      x[k] = x0[k];
+      v[k] = constrained(m, dim, g, c) ? 0.0 : vv[c];
+    }
+  }
+}
+
+// out[e][j] = sum_k Me_inv[e][j][k] rhs[e][k]
+__global__ void k_energy_solve(int ne, int nl, const double *__restrict__ me_inv, const double *__restrict__ rhs,
+                               double *__restrict__ out) {
+  const size_t n = (size_t)ne * nl;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = k / nl;
+    const double *Mi = me_inv + k * nl;
+    const double *r = rhs + e * nl;
+    double s = Mi[0] * r[0];
+    for (int j = 1; j < nl; ++j) s = fma(Mi[j], r[j], s);
+    out[k] = s;
+  }
+}
+
+// Stage-1 state update of RK2-average: vb0 = v + dt/2 a0, v_h = vb0, x_h = x + dt/2 vb0.
+__global__ void k_rk_mid(size_t nv, const double *__restrict__ x, const double *__restrict__ v,
+                         const double *__restrict__ a0, const double *__restrict__ dtp, double *__restrict__ xh,
+                         double *__restrict__ vh) {
+  const double hdt = 0.5 * *dtp;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (size_t)gridDim.x * blockDim.x) {
+    const double vb = fma(hdt, a0[k], v[k]);
+    vh[k] = vb;
+    xh[k] = fma(hdt, vb, x[k]);
+  }
+}
+
+// Final update: vb = v + dt/2 a, x += dt vb, v += dt a.
+__global__ void k_rk_final(size_t nv, double *__restrict__ x, double *__restrict__ v, const double *__restrict__ a,
+                           const double *__restrict__ dtp, double *__restrict__ vbo) {
+  const double dt = *dtp, hdt = 0.5 * dt;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (size_t)gridDim.x * blockDim.x) {
+    const double ak = a[k], vk = v[k];
+    const double vb = fma(hdt, ak, vk);
+    vbo[k] = vb;
+    x[k] = fma(dt, vb, x[k]);
+    v[k] = fma(dt, ak, vk);
+  }
+}
+
+__global__ void k_step_finish(lh_step_info *info, const int *status, int has_source) {
+  info->t += info->dt;
+  info->steps += 1;
+  info->status = *status;
+  if (!has_source) info->energy_src = 0.0;
+}
+
+inline int grid_for(size_t n, int threads, int cap) {
+  size_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > (size_t)cap) g = cap;
+  return (int)g;
+}
+
+thread_local std::string g_setup_error = "no error";
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct lh_ctx {
+  lh_params prm{};
+  MeshDesc mesh{};
+  const Ops *ops = nullptr;
+  int dim = 0, p = 0, q1 = 0, nd = 0, nl = 0, nq = 0;
+  size_t nv = 0;
+  int grid_elem = 0, grid_cg = 0, grid_node = 0, sms = 0;
+  double h0 = 0.0, volume = 0.0;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  // sub-buffers
+  double *tab = nullptr, *verts = nullptr, *x0 = nullptr, *rho0 = nullptr, *mq = nullptr, *jinv0 = nullptr,
+         *D = nullptr, *me_inv = nullptr, *invdiag = nullptr, *evec = nullptr, *r = nullptr, *pv = nullptr,
+         *ap = nullptr, *a_prev = nullptr, *rhs = nullptr, *xh = nullptr, *vh = nullptr, *vb = nullptr,
+         *eh = nullptr, *partials = nullptr;
+  unsigned int *counter = nullptr;
+  GridBarrier *bar = nullptr;
+  int *dstatus = nullptr;
+  std::string err = "no error";
+};
+
+static lh_status fail(lh_ctx *c, lh_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_setup_error = msg;
+  return s;
+}
+
+static lh_status check_launch(lh_ctx *c, const char *what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, LH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return LH_OK;
+}
+
+#define LH_CUDA(c, call)                                                                    \
+  do {                                                                                      \
+    cudaError_t _e = (call);                                                                \
+    if (_e != cudaSuccess) return fail((c), LH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+extern "C" {
+
+void lh_destroy(lh_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->arena) cudaFree(ctx->arena);
+  delete ctx;
+}
+
+const char *lh_last_error(const lh_ctx *ctx) { return ctx ? ctx->err.c_str() : g_setup_error.c_str(); }
+
+lh_status lh_get_sizes(const lh_ctx *ctx, lh_sizes *out) {
+  if (!ctx || !out) return LH_ERR_ARG;
+  out->ne = ctx->mesh.ne;
+  out->n_h1 = ctx->mesh.nh1;
+  out->nv = (int64_t)ctx->nv;
+  out->n_l2 = (int64_t)ctx->mesh.ne * ctx->nl;
+  out->nq = (int64_t)ctx->mesh.ne * ctx->nq;
+  out->arena_bytes = (int64_t)ctx->arena_bytes;
+  return LH_OK;
+}
+
+static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_q) {
+  const int dim = prm->dim, p = prm->order, q1 = prm->q1;
+  c->prm = *prm;
+  c->prm.vertices = nullptr;
+  c->dim = dim;
+  c->p = p;
+  c->q1 = q1;
+  c->ops = dim == 2 ? find_ops_2d(p, q1) : find_ops_3d(p, q1);
+  if (!c->ops) return fail(c, LH_ERR_UNSUPPORTED, "no compiled kernels for this (dim, order, q1)");
+  MeshDesc &m = c->mesh;
+  m.nx = prm->nx;
+  m.ny = prm->ny;
+  m.nz = dim == 3 ? prm->nz : 1;
+  m.n1x = m.nx * p + 1;
+  m.n1y = m.ny * p + 1;
+  m.n1z = dim == 3 ? m.nz * p + 1 : 1;
+  const double ne_d = (double)m.nx * m.ny * m.nz;
+  const double nh1_d = (double)m.n1x * m.n1y * m.n1z;
+  c->nd = 1; c->nl = 1; c->nq = 1;
+  for (int a = 0; a < dim; ++a) { c->nd *= p + 1; c->nl *= p; c->nq *= q1; }
+  if (ne_d * c->nq * dim * dim > 2.0e9 || nh1_d * dim > 2.0e9)
+    return fail(c, LH_ERR_ARG, "mesh too large for 32-bit indexing");
+  m.ne = m.nx * m.ny * m.nz;
+  m.nh1 = m.n1x * m.n1y * m.n1z;
+  c->nv = (size_t)dim * m.nh1;
+
+  int dev = 0;
+  LH_CUDA(c, cudaGetDevice(&dev));
+  LH_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  const Ops &o = *c->ops;
+  const size_t smems[] = {o.smem_qdata, o.smem_force, o.smem_force_t, o.smem_mass, o.smem_cg,
+                          o.smem_geom,  o.smem_diag,  o.smem_emass,   o.smem_init_e};
+  void *kerns[] = {o.k_qdata, o.k_force, o.k_force_t, o.k_mass, o.k_cg, o.k_geom, o.k_diag, o.k_emass, o.k_init_e};
+  for (int k = 0; k < 9; ++k)
+    LH_CUDA(c, cudaFuncSetAttribute(kerns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smems[k]));
+  c->grid_elem = (m.ne + o.nb - 1) / o.nb;
+  int occ = 0;
+  LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, o.k_cg, o.threads, o.smem_cg));
+  if (occ < 1) return fail(c, LH_ERR_CUDA, "CG kernel cannot be resident");
+  {
+    const int want = std::max(c->grid_elem, grid_for(c->nv, o.threads, 1 << 30));
+    c->grid_cg = std::min(occ * c->sms, want);
+  }
+  c->grid_node = grid_for(c->nv, kNodeThreads, 8 * c->sms * 8);
+
+  // ---- arena
+  const size_t NE = m.ne, NQ = c->nq, NH1 = m.nh1, NV = c->nv;
+  const int tablen = table_length(p, q1);
+  const size_t nverts = (size_t)(m.nx + 1) * (m.ny + 1) * (dim == 3 ? m.nz + 1 : 1);
+  const size_t npart = 4 * (size_t)std::max(c->grid_elem, c->grid_cg);
+  struct Item { double **ptr; size_t n; };
+  std::vector<Item> items = {
+      {&c->tab, (size_t)tablen},       {&c->verts, nverts * dim},   {&c->x0, NV},
+      {&c->rho0, NE * NQ},             {&c->mq, NE * NQ},           {&c->jinv0, NE * dim * dim * NQ},
+      {&c->D, NE * dim * dim * NQ},    {&c->me_inv, NE * c->nl * c->nl}, {&c->invdiag, NV},
+      {&c->evec, NE * dim * c->nd},    {&c->r, NV},                 {&c->pv, NV},
+      {&c->ap, NV},                    {&c->a_prev, NV},            {&c->rhs, NV},
+      {&c->xh, NV},                    {&c->vh, NV},                {&c->vb, NV},
+      {&c->eh, NE * c->nl},            {&c->partials, npart}};
+  size_t bytes = 0;
+  for (auto &it : items) bytes += (it.n * sizeof(double) + 255) / 256 * 256;
+  const size_t ctl_bytes = 256;
+  bytes += ctl_bytes;
+  cudaError_t e = cudaMalloc(&c->arena, bytes);
+  if (e != cudaSuccess) {
+    c->arena = nullptr;
+    return fail(c, LH_ERR_OOM, std::string("arena allocation of ") + std::to_string(bytes) + " bytes failed");
+  }
+  c->arena_bytes = bytes;
+  LH_CUDA(c, cudaMemset(c->arena, 0, bytes));
+  size_t off = 0;
+  for (auto &it : items) {
+    *it.ptr = (double *)(c->arena + off);
+    off += (it.n * sizeof(double) + 255) / 256 * 256;
+  }
+  char *ctl = c->arena + off;
+  c->counter = (unsigned int *)ctl;
+  c->bar = (GridBarrier *)(ctl + 64);
+  c->dstatus = (int *)(ctl + 128);
+
+  // ---- tables, vertices, node positions
+  std::vector<double> tab(tablen);
+  try {
+    build_tables(p, q1, tab.data(), tablen);
+  } catch (const std::exception &ex) {
+    return fail(c, LH_ERR_ARG, ex.what());
+  }
+  LH_CUDA(c, cudaMemcpy(c->tab, tab.data(), tablen * sizeof(double), cudaMemcpyHostToDevice));
+  LH_CUDA(c, cudaMemcpy(c->verts, prm->vertices, nverts * dim * sizeof(double), cudaMemcpyHostToDevice));
+  Zs z{};
+  gll_nodes(p, z.z);
+  k_nodes_x0<<<grid_for(NH1, kNodeThreads, 65535), kNodeThreads>>>(m, dim, p, z, c->verts, c->x0);
+  if (lh_status s = check_launch(c, "nodes")) return s;
+
+  // ---- geometry at qpoints
+  GeomArgs ga{m, c->tab, c->x0, rho0_q, c->rho0, c->mq, c->jinv0, c->partials, c->dstatus};
+  o.geom(ga, c->grid_elem, 0);
+  if (lh_status s = check_launch(c, "geometry")) return s;
+  LH_CUDA(c, cudaDeviceSynchronize());
+  int st = 0;
+  LH_CUDA(c, cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st == LH_ERR_INVERTED) return fail(c, LH_ERR_INVERTED, "det J0 <= 0 in the initial mesh");
+  std::vector<double> part(c->grid_elem);
+  LH_CUDA(c, cudaMemcpy(part.data(), c->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  double vol = 0.0;
+  for (double v : part) vol += v;
+  c->volume = vol;
+  c->h0 = std::pow(vol / (double)m.ne, 1.0 / dim) / p;
+
+  // ---- energy-mass inverses, Jacobi diagonal
+  EmassArgs ea{c->tab, c->mq, c->me_inv};
+  o.emass(ea, m.ne, 0);
+  if (lh_status s = check_launch(c, "energy mass")) return s;
+  DiagArgs da{m, c->tab, c->mq, c->evec};
+  o.diag(da, c->grid_elem, 0);
+  if (lh_status s = check_launch(c, "diag")) return s;
+  o.gather(m, c->evec, 1, c->r, 1.0, nullptr, c->grid_node, kNodeThreads, 0);
+  if (lh_status s = check_launch(c, "diag gather")) return s;
+  k_invdiag<<<c->grid_node, kNodeThreads>>>(m, dim, c->r, c->invdiag);
+  if (lh_status s = check_launch(c, "invdiag")) return s;
+  LH_CUDA(c, cudaMemset(c->r, 0, NV * sizeof(double)));
+  LH_CUDA(c, cudaDeviceSynchronize());
+  return LH_OK;
+}
+
+lh_status lh_setup(const lh_params *prm, const double *rho0_q, lh_ctx **out) {
+  if (!out) return fail(nullptr, LH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!prm || !prm->vertices) return fail(nullptr, LH_ERR_ARG, "params or vertices is NULL");
+  if (prm->dim != 2 && prm->dim != 3) return fail(nullptr, LH_ERR_ARG, "dim must be 2 or 3");
+  if (prm->nx < 1 || prm->ny < 1 || (prm->dim == 3 && prm->nz < 1))
+    return fail(nullptr, LH_ERR_ARG, "element counts must be >= 1");
+  if (prm->order < 1 || prm->order > 4) return fail(nullptr, LH_ERR_ARG, "order must be in 1..4");
+  if (prm->q1 < 1 || prm->q1 > 8) return fail(nullptr, LH_ERR_ARG, "q1 must be in 1..8");
+  if (!(prm->gamma > 1.0)) return fail(nullptr, LH_ERR_ARG, "gamma must be > 1");
+  if (!(prm->cfl > 0.0)) return fail(nullptr, LH_ERR_ARG, "cfl must be > 0");
+  if (prm->source != LH_SOURCE_NONE && prm->source != LH_SOURCE_TAYLOR_GREEN_2D)
+    return fail(nullptr, LH_ERR_ARG, "unknown source");
+  if (prm->source == LH_SOURCE_TAYLOR_GREEN_2D && prm->dim != 2)
+    return fail(nullptr, LH_ERR_ARG, "the Taylor-Green source is 2D only");
+  if (prm->precision != LH_PRECISION_FP64 && prm->precision != LH_PRECISION_FP32_IR)
+    return fail(nullptr, LH_ERR_ARG, "unknown precision");
+  lh_ctx *c = new lh_ctx();
+  const lh_status s = setup_impl(c, prm, rho0_q);
+  if (s != LH_OK) {
+    g_setup_error = c->err;
+    lh_destroy(c);
+    return s;
+  }
+  *out = c;
+  return LH_OK;
+}
+
+lh_status lh_sync_status(lh_ctx *ctx) {
+  if (!ctx) return LH_ERR_ARG;
+  LH_CUDA(ctx, cudaDeviceSynchronize());
+  int st = 0;
+  LH_CUDA(ctx, cudaMemcpy(&st, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  LH_CUDA(ctx, cudaMemset(ctx->dstatus, 0, sizeof(int)));
+  if (st != 0) {
+    static const char *names[] = {"ok", "argument", "cuda", "out of memory", "inverted element (det J <= 0)",
+                                  "CG not converged", "device wait timed out", "unsupported"};
+    ctx->err = std::string("device status: ") + (st >= 0 && st < 8 ? names[st] : "unknown");
+  }
+  return (lh_status)st;
+}
+
+lh_status lh_init_state(lh_ctx *ctx, int problem, double *x, double *v, double *e, lh_stream_t stream) {
+  if (!ctx || !x || !v || !e) return ctx ? fail(ctx, LH_ERR_ARG, "null state pointer") : LH_ERR_ARG;
+  if (problem != LH_PROBLEM_TAYLOR_GREEN && problem != LH_PROBLEM_GRESHO)
+    return fail(ctx, LH_ERR_ARG, "unknown problem");
+  if (problem == LH_PROBLEM_GRESHO && ctx->dim != 2) return fail(ctx, LH_ERR_ARG, "Gresho is 2D only");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_init_v<<<grid_for(ctx->mesh.nh1, kNodeThreads, 65535), kNodeThreads, 0, s>>>(ctx->mesh, ctx->dim, problem,
+                                                                                  ctx->x0, x, v);
+  if (lh_status st = check_launch(ctx, "init v")) return st;
+  InitEArgs ia{ctx->mesh, ctx->tab, ctx->x0, ctx->mq, ctx->rho0, ctx->me_inv, e, ctx->prm.gamma, problem};
+  ctx->ops->init_e(ia, ctx->grid_elem, s);
+  return check_launch(ctx, "init e");
+}
+
+static void fill_qdata(lh_ctx *c, QdataArgs &a, const double *x, const double *v, const double *e) {
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.x = x;
+  a.v = v;
+  a.e = e;
+  a.mq = c->mq;
+  a.jinv0 = c->jinv0;
+  a.D = c->D;
+  a.phys.gamma = c->prm.gamma;
+  a.phys.h0 = c->h0;
+  a.phys.order = (double)c->p;
+  a.phys.use_viscosity = c->prm.use_viscosity;
+  a.want_dt = 0;
+  a.cfl = c->prm.cfl;
+  a.fixed_dt = 0.0;
+  a.partials = c->partials;
+  a.counter = c->counter;
+  a.dt_est_out = nullptr;
+  a.step = nullptr;
+  a.status = c->dstatus;
+}
+
+lh_status lh_update_qdata(lh_ctx *ctx, const double *x, const double *v, const double *e, double *dt_est,
+                          lh_stream_t stream) {
+  if (!ctx || !x || !v || !e) return ctx ? fail(ctx, LH_ERR_ARG, "null state pointer") : LH_ERR_ARG;
+  QdataArgs a;
+  fill_qdata(ctx, a, x, v, e);
+  a.want_dt = dt_est != nullptr;
+  a.dt_est_out = dt_est;
+  ctx->ops->qdata(a, ctx->grid_elem, (cudaStream_t)stream);
+  return check_launch(ctx, "qdata");
+}
+
+lh_status lh_copy_qdata(lh_ctx *ctx, double *out, lh_stream_t stream) {
+  if (!ctx || !out) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  LH_CUDA(ctx, cudaMemcpyAsync(out, ctx->D, (size_t)ctx->mesh.ne * ctx->dim * ctx->dim * ctx->nq * sizeof(double),
+                               cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return LH_OK;
+}
+
+static lh_status force_impl(lh_ctx *c, const double *u, double *out, double scale, const double *mask,
+                            cudaStream_t s) {
+  ForceArgs fa{c->mesh, c->tab, c->D, u, c->evec};
+  c->ops->force(fa, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "force")) return st;
+  c->ops->gather(c->mesh, c->evec, c->dim, out, scale, mask, c->grid_node, kNodeThreads, s);
+  return check_launch(c, "force gather");
+}
+
+lh_status lh_force_mult(lh_ctx *ctx, const double *u, double *rhs, lh_stream_t stream) {
+  if (!ctx || !rhs) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  return force_impl(ctx, u, rhs, 1.0, nullptr, (cudaStream_t)stream);
+}
+
+lh_status lh_force_mult_t(lh_ctx *ctx, const double *v, double *out, lh_stream_t stream) {
+  if (!ctx || !v || !out) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  ForceTArgs a{};
+  a.mesh = ctx->mesh;
+  a.tab = ctx->tab;
+  a.D = ctx->D;
+  a.v = v;
+  a.mq = ctx->mq;
+  a.out = out;
+  ctx->ops->force_t(a, ctx->grid_elem, (cudaStream_t)stream);
+  return check_launch(ctx, "force_t");
+}
+
+lh_status lh_mass_mult(lh_ctx *ctx, const double *x, double *y, lh_stream_t stream) {
+  if (!ctx || !x || !y) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (x == y) return fail(ctx, LH_ERR_ARG, "x and y must not alias");
+  MassArgs a{ctx->mesh, ctx->tab, ctx->mq, x, ctx->evec};
+  ctx->ops->mass(a, ctx->grid_elem, (cudaStream_t)stream);
+  if (lh_status st = check_launch(ctx, "mass")) return st;
+  ctx->ops->gather(ctx->mesh, ctx->evec, ctx->dim, y, 1.0, nullptr, ctx->grid_node, kNodeThreads,
+                   (cudaStream_t)stream);
+  return check_launch(ctx, "mass gather");
+}
+
+static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
+                         int *iters_out, double *relres_out, cudaStream_t s) {
+  CgArgs a{};
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.mq = c->mq;
+  a.invdiag = c->invdiag;
+  a.b = b;
+  a.x = x;
+  a.r = c->r;
+  a.p = c->pv;
+  a.ap = c->ap;
+  a.evec = c->evec;
+  a.partials = c->partials;
+  a.bar = c->bar;
+  a.status = c->dstatus;
+  a.info = info;
+  a.iters_out = iters_out;
+  a.relres_out = relres_out;
+  a.tol = tol;
+  a.max_it = max_it;
+  const cudaError_t e = c->ops->cg(a, c->grid_cg, s);
+  if (e != cudaSuccess) return fail(c, LH_ERR_CUDA, std::string("cg launch: ") + cudaGetErrorString(e));
+  return check_launch(c, "cg");
+}
+
+lh_status lh_mass_cg(lh_ctx *ctx, const double *b, double *x, double rel_tol, int max_it, lh_cg_info *info,
+                     lh_stream_t stream) {
+  if (!ctx || !b || !x) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (!(rel_tol >= 0.0) || max_it < 0) return fail(ctx, LH_ERR_ARG, "bad tolerance or iteration limit");
+  if (b == x) return fail(ctx, LH_ERR_ARG, "b and x must not alias");
+  return cg_impl(ctx, b, x, rel_tol, max_it, info, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+lh_status lh_energy_solve(lh_ctx *ctx, const double *rhs, double *out, lh_stream_t stream) {
+  if (!ctx || !rhs || !out) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (rhs == out) return fail(ctx, LH_ERR_ARG, "rhs and out must not alias");
+  const size_t n = (size_t)ctx->mesh.ne * ctx->nl;
+  k_energy_solve<<<grid_for(n, kNodeThreads, 65535), kNodeThreads, 0, (cudaStream_t)stream>>>(
+      ctx->mesh.ne, ctx->nl, ctx->me_inv, rhs, out);
+  return check_launch(ctx, "energy solve");
+}
+
+lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt, double rel_tol, int max_it,
+                         lh_step_info *info, lh_stream_t stream) {
+  if (!ctx || !x || !v || !e || !info) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (rel_tol <= 0.0) rel_tol = 1e-12;
+  if (max_it <= 0) max_it = 1000;
+  cudaStream_t s = (cudaStream_t)stream;
+  lh_ctx *c = ctx;
+  const Ops &o = *c->ops;
+  const double *dtp = &info->dt;
+  const bool src = c->prm.source == LH_SOURCE_TAYLOR_GREEN_2D;
+  // ---- stage 1 at S_n
+  QdataArgs qa;
+  fill_qdata(c, qa, x, v, e);
+  qa.want_dt = 1;
+  qa.fixed_dt = dt;
+  qa.step = info;
+  o.qdata(qa, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "qdata 1")) return st;
+  if (lh_status st = force_impl(c, nullptr, c->rhs, -1.0, c->invdiag, s)) return st;
+  if (lh_status st = cg_impl(c, c->rhs, c->a_prev, rel_tol, max_it, nullptr, &info->cg_iters[0],
+                             &info->cg_rel_res[0], s))
+    return st;
+  k_rk_mid<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x, v, c->a_prev, dtp, c->xh, c->vh);
+  if (lh_status st = check_launch(c, "rk mid")) return st;
+  ForceTArgs fa{};
+  fa.mesh = c->mesh;
+  fa.tab = c->tab;
+  fa.D = c->D;
+  fa.v = c->vh;
+  fa.mq = c->mq;
+  fa.src_x = src ? x : nullptr;
+  fa.me_inv = c->me_inv;
+  fa.e_base = e;
+  fa.dt = dtp;
+  fa.coef = 0.5;
+  fa.out = c->eh;
+  o.force_t(fa, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "force_t 1")) return st;
+  // ---- stage 2 at S_half
+  fill_qdata(c, qa, c->xh, c->vh, c->eh);
+  o.qdata(qa, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "qdata 2")) return st;
+  if (lh_status st = force_impl(c, nullptr, c->rhs, -1.0, c->invdiag, s)) return st;
+  if (lh_status st = cg_impl(c, c->rhs, c->a_prev, rel_tol, max_it, nullptr, &info->cg_iters[1],
+                             &info->cg_rel_res[1], s))
+    return st;
+  k_rk_final<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x, v, c->a_prev, dtp, c->vb);
+  if (lh_status st = check_launch(c, "rk final")) return st;
+  fa.v = c->vb;
+  fa.src_x = src ? c->xh : nullptr;
+  fa.coef = 1.0;
+  fa.out = e;
+  fa.partials = c->partials;
+  fa.counter = c->counter;
+  fa.src_sum = src ? &info->energy_src : nullptr;
+  o.force_t(fa, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "force_t 2")) return st;
+  k_step_finish<<<1, 1, 0, s>>>(info, c->dstatus, src ? 1 : 0);
+  return check_launch(c, "step finish");
+}
+
+}  // extern "C"

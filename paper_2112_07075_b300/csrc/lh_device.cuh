@@ -71,25 +71,35 @@ __device__ __forceinline__ void contract2(const double *__restrict__ in1, const 
 }
 
 // ---------------------------------------------------------------------------
+// Scratch sizes (doubles) of the helpers below, for C tensors.
+// ---------------------------------------------------------------------------
+template <int DIM, int NI, int NO>
+__host__ __device__ constexpr int interp_scratch(int C) {
+  return DIM == 2 ? C * NI * NO : C * NI * NO * (NI + NO);
+}
+template <int DIM, int D, int Q>
+__host__ __device__ constexpr int grad_scratch(int C) {
+  return DIM == 2 ? 2 * C * D * Q : 2 * C * D * D * Q + 3 * C * D * Q * Q;
+}
+
+// ---------------------------------------------------------------------------
 // Full tensor-product interpolation with one 1D matrix M [NO][NI] on every axis:
 //   out[c][o_z][o_y][o_x] = sum M[o_x][i_x] M[o_y][i_y] M[o_z][i_z] in[c][i_z][i_y][i_x]
-// for C independent tensors. t1, t2: scratch of C * max(NI,NO)^DIM doubles each.
-// Ends with a __syncthreads.
+// for C independent tensors. S: interp_scratch(C) doubles. Ends with a __syncthreads.
 // ---------------------------------------------------------------------------
 template <int DIM, int NI, int NO, int C>
 __device__ __forceinline__ void interp(const double *__restrict__ in, double *__restrict__ out,
-                                       double *__restrict__ t1, double *__restrict__ t2,
-                                       const double *__restrict__ M) {
+                                       double *__restrict__ S, const double *__restrict__ M) {
   if constexpr (DIM == 2) {
-    contract<C * NI, NI, NO, 1>(in, t1, M);         // x: [C][iy][ox]
+    contract<C * NI, NI, NO, 1>(in, S, M);          // x: [C][iy][ox]
     __syncthreads();
-    contract<C, NI, NO, NO>(t1, out, M);            // y: [C][oy][ox]
+    contract<C, NI, NO, NO>(S, out, M);             // y: [C][oy][ox]
     __syncthreads();
-    (void)t2;
   } else {
-    contract<C * NI * NI, NI, NO, 1>(in, t1, M);    // x: [C][iz][iy][ox]
+    double *t2 = S + C * NI * NI * NO;
+    contract<C * NI * NI, NI, NO, 1>(in, S, M);     // x: [C][iz][iy][ox]
     __syncthreads();
-    contract<C * NI, NI, NO, NO>(t1, t2, M);        // y: [C][iz][oy][ox]
+    contract<C * NI, NI, NO, NO>(S, t2, M);         // y: [C][iz][oy][ox]
     __syncthreads();
     contract<C, NI, NO, NO * NO>(t2, out, M);       // z: [C][oz][oy][ox]
     __syncthreads();
@@ -99,26 +109,25 @@ __device__ __forceinline__ void interp(const double *__restrict__ in, double *__
 // ---------------------------------------------------------------------------
 // Reference gradient at quadrature points of C scalar H1 tensors:
 //   g[l][c][q] = sum_i dw_i/dxi_l(q) u[c][i],  B, G: [Q][D].
-// Scratch (3D): ta, tb: C*D*D*Q each; tc, td, te: C*D*Q*Q each.
-// Scratch (2D): ta, tb: C*D*Q each.
-// Ends with a __syncthreads. FP64 cost per tensor (3D): 2QD^3 + 3Q^2D^2 + 3Q^3D.
+// S: grad_scratch(C) doubles. Ends with a __syncthreads.
+// FP64 cost per tensor (3D): 2QD^3 + 3Q^2D^2 + 3Q^3D fused multiply-adds.
 // ---------------------------------------------------------------------------
 template <int DIM, int D, int Q, int C>
 __device__ __forceinline__ void grad_ref(const double *__restrict__ u, double *__restrict__ g,
-                                         double *__restrict__ ta, double *__restrict__ tb,
-                                         double *__restrict__ tc, double *__restrict__ td,
-                                         double *__restrict__ te, const double *__restrict__ B,
+                                         double *__restrict__ S, const double *__restrict__ B,
                                          const double *__restrict__ G) {
   constexpr int NQ = ipow<Q, DIM>::value;
   if constexpr (DIM == 2) {
-    contract<C * D, D, Q, 1>(u, ta, B);   // [C][iy][qx] B_x
-    contract<C * D, D, Q, 1>(u, tb, G);   // [C][iy][qx] G_x
+    double *ta = S, *tb = S + C * D * Q;
+    contract<C * D, D, Q, 1>(u, ta, B);       // [C][iy][qx] B_x
+    contract<C * D, D, Q, 1>(u, tb, G);       // [C][iy][qx] G_x
     __syncthreads();
     contract<C, D, Q, Q>(tb, g, B);           // d/dx: G_x B_y
     contract<C, D, Q, Q>(ta, g + C * NQ, G);  // d/dy: B_x G_y
     __syncthreads();
-    (void)tc; (void)td; (void)te;
   } else {
+    double *ta = S, *tb = ta + C * D * D * Q, *tc = tb + C * D * D * Q;
+    double *td = tc + C * D * Q * Q, *te = td + C * D * Q * Q;
     contract<C * D * D, D, Q, 1>(u, ta, B);   // [C][iz][iy][qx] B_x
     contract<C * D * D, D, Q, 1>(u, tb, G);   // G_x
     __syncthreads();
@@ -136,26 +145,24 @@ __device__ __forceinline__ void grad_ref(const double *__restrict__ u, double *_
 // ---------------------------------------------------------------------------
 // Transposed reference gradient: for C components,
 //   y[c][i] = sum_q sum_l dw_i/dxi_l(q) f[l][c][q],   f: [DIM][C][Q^DIM]
-// Bt, Gt: [D][Q] (transposed tables).
-// Scratch (3D): ta, tb, tc: C*D*Q*Q each; td, te: C*D*D*Q each.
-// Scratch (2D): ta, tb: C*D*Q each. Ends with a __syncthreads.
-// FP64 cost per component (3D): 3Q^3D + 3Q^2D^2 + 2QD^3.
+// Bt, Gt: [D][Q] (transposed tables). S: grad_scratch(C) doubles.
+// Ends with a __syncthreads. FP64 cost per component (3D): 3Q^3D + 3Q^2D^2 + 2QD^3.
 // ---------------------------------------------------------------------------
 template <int DIM, int D, int Q, int C>
 __device__ __forceinline__ void grad_ref_t(const double *__restrict__ f, double *__restrict__ y,
-                                           double *__restrict__ ta, double *__restrict__ tb,
-                                           double *__restrict__ tc, double *__restrict__ td,
-                                           double *__restrict__ te, const double *__restrict__ Bt,
+                                           double *__restrict__ S, const double *__restrict__ Bt,
                                            const double *__restrict__ Gt) {
   constexpr int NQ = ipow<Q, DIM>::value;
   if constexpr (DIM == 2) {
+    double *ta = S, *tb = S + C * D * Q;
     contract<C, Q, D, Q>(f, ta, Bt);            // [C][iy][qx]: B_y^T f_x
     contract<C, Q, D, Q>(f + C * NQ, tb, Gt);   // G_y^T f_y
     __syncthreads();
     contract2<C * D, Q, D, 1>(ta, Gt, tb, Bt, y);  // x: G_x^T (.) + B_x^T (.)
     __syncthreads();
-    (void)tc; (void)td; (void)te;
   } else {
+    double *ta = S, *tb = ta + C * D * Q * Q, *tc = tb + C * D * Q * Q;
+    double *td = tc + C * D * Q * Q, *te = td + C * D * D * Q;
     contract<C, Q, D, Q * Q>(f, ta, Bt);               // [C][iz][qy][qx]: B_z^T f_x
     contract<C, Q, D, Q * Q>(f + C * NQ, tb, Bt);      // B_z^T f_y
     contract<C, Q, D, Q * Q>(f + 2 * C * NQ, tc, Gt);  // G_z^T f_z

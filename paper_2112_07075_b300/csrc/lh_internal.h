@@ -1,0 +1,130 @@
+// Internal types of liblh shared by the host API and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/lh.h"
+
+namespace lh {
+
+struct MeshDesc {
+  int nx, ny, nz;      // elements per direction (nz = 1 in 2D)
+  int n1x, n1y, n1z;   // H1 nodes per direction
+  int ne;              // elements
+  int nh1;             // scalar H1 nodes
+};
+
+struct PhysParams {
+  double gamma;
+  double h0;           // (|Omega_0| / NE)^(1/dim) / p
+  double order;        // p, for hmin = sigma_min(J) / p
+  int use_viscosity;
+};
+
+struct QdataArgs {
+  MeshDesc mesh;
+  const double *tab, *x, *v, *e, *mq, *jinv0;
+  double *D;
+  PhysParams phys;
+  int want_dt;
+  double cfl, fixed_dt;
+  double *partials;          // [gridDim] block maxima of 1/dt
+  unsigned int *counter;     // last-block ticket (reset by the last block)
+  double *dt_est_out;        // optional
+  lh_step_info *step;        // optional: dt control of lh_rk2avg_step
+  int *status;
+};
+
+struct ForceArgs {
+  MeshDesc mesh;
+  const double *tab, *D, *u;
+  double *evec;              // [NE][DIM][ND]
+};
+
+struct ForceTArgs {
+  MeshDesc mesh;
+  const double *tab, *D, *v, *mq;
+  const double *src_x;       // positions for the TG-2D energy source, or NULL
+  const double *me_inv;      // NULL: out = F^T v; else out = e_base + coef*dt*Me^{-1}(F^T v + b)
+  const double *e_base, *dt;
+  double coef;
+  double *out;
+  double *partials;          // for the source sum
+  unsigned int *counter;
+  double *src_sum;           // optional: dt * sum_j b_j
+};
+
+struct MassArgs {
+  MeshDesc mesh;
+  const double *tab, *mq, *x;
+  double *evec;
+};
+
+struct CgArgs {
+  MeshDesc mesh;
+  const double *tab, *mq, *invdiag, *b;
+  double *x, *r, *p, *ap, *evec, *partials;
+  void *bar;                 // GridBarrier
+  int *status;
+  lh_cg_info *info;
+  int *iters_out;
+  double *relres_out;
+  double tol;
+  int max_it;
+};
+
+struct GeomArgs {
+  MeshDesc mesh;
+  const double *tab, *x0, *rho0_in;
+  double *rho0, *mq, *jinv0, *partials;
+  int *status;
+};
+
+struct DiagArgs {
+  MeshDesc mesh;
+  const double *tab, *mq;
+  double *evec;              // [NE][ND]
+};
+
+struct EmassArgs {
+  const double *tab, *mq;
+  double *me_inv;
+};
+
+struct InitEArgs {
+  MeshDesc mesh;
+  const double *tab, *x0, *mq, *rho0, *me_inv;
+  double *e;
+  double gamma;
+  int problem;
+};
+
+// Launchers of one compiled (dim, p, q1) family.
+struct Ops {
+  int dim, p, q1, nb, threads;
+  size_t smem_qdata, smem_force, smem_force_t, smem_mass, smem_cg, smem_geom, smem_diag, smem_emass, smem_init_e;
+  void *k_qdata, *k_force, *k_force_t, *k_mass, *k_cg, *k_geom, *k_diag, *k_emass, *k_init_e;
+  void (*qdata)(const QdataArgs &, int grid, cudaStream_t);
+  void (*force)(const ForceArgs &, int grid, cudaStream_t);
+  void (*force_t)(const ForceTArgs &, int grid, cudaStream_t);
+  void (*mass)(const MassArgs &, int grid, cudaStream_t);
+  cudaError_t (*cg)(CgArgs &, int grid, cudaStream_t);
+  void (*geom)(const GeomArgs &, int grid, cudaStream_t);
+  void (*diag)(const DiagArgs &, int grid, cudaStream_t);
+  void (*emass)(const EmassArgs &, int grid, cudaStream_t);
+  void (*init_e)(const InitEArgs &, int grid, cudaStream_t);
+  void (*gather)(const MeshDesc &, const double *evec, int C, double *out, double scale, const double *mask,
+                 int grid, int threads, cudaStream_t);
+};
+
+const Ops *find_ops_2d(int p, int q1);
+const Ops *find_ops_3d(int p, int q1);
+
+// Host-side 1D tables (basis_host.cpp): fills tab in the layout the kernels expect.
+void build_tables(int p, int q1, double *tab, int tab_len);
+int table_length(int p, int q1);
+void gll_nodes(int p, double *z);
+
+}  // namespace lh

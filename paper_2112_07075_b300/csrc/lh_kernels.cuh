@@ -1,0 +1,939 @@
+// Templated CUDA kernels of liblh for one (DIM, P, Q) = (dimension, H1 order,
+// Gauss points per direction) combination. Every kernel is element-batched:
+// a CTA owns NB consecutive elements, stages their DOFs and quadrature data in
+// shared memory and applies the 1D basis tables one axis at a time (sum
+// factorization, arXiv 2112.07075 Section 3.2). Element results that belong to
+// shared H1 nodes go to an element vector (E-vector) and are summed per node by
+// a deterministic gather (the G^T of Section 3.1), so results are bit-identical
+// from run to run.
+#pragma once
+
+#include "lh_device.cuh"
+#include "lh_internal.h"
+
+namespace lh {
+
+// ---------------------------------------------------------------------------
+// Structured-mesh index maps (layouts documented in include/lh.h).
+// ---------------------------------------------------------------------------
+template <int DIM, int D>
+__device__ __forceinline__ int h1_node(const MeshDesc &m, int e, int i) {
+  constexpr int P = D - 1;
+  const int ex = e % m.nx;
+  const int t = e / m.nx;
+  const int ix = i % D;
+  if constexpr (DIM == 2) {
+    const int ey = t;
+    const int iy = i / D;
+    return (ex * P + ix) + m.n1x * (ey * P + iy);
+  } else {
+    const int ey = t % m.ny, ez = t / m.ny;
+    const int iy = (i / D) % D, iz = i / (D * D);
+    return (ex * P + ix) + m.n1x * ((ey * P + iy) + m.n1y * (ez * P + iz));
+  }
+}
+
+// Is H1 node g constrained for velocity component c (v.n = 0 on the box faces)?
+template <int DIM>
+__device__ __forceinline__ bool h1_constrained(const MeshDesc &m, int g, int c) {
+  const int gx = g % m.n1x;
+  if (c == 0) return gx == 0 || gx == m.n1x - 1;
+  const int t = g / m.n1x;
+  if constexpr (DIM == 2) {
+    return t == 0 || t == m.n1y - 1;
+  } else {
+    if (c == 1) {
+      const int gy = t % m.n1y;
+      return gy == 0 || gy == m.n1y - 1;
+    }
+    const int gz = t / m.n1y;
+    return gz == 0 || gz == m.n1z - 1;
+  }
+}
+
+// Contributions of element-local nodes to H1 node coordinate gc along one axis.
+__device__ __forceinline__ int axis_owners(int gc, int P, int nel, int (&ee)[2], int (&ii)[2]) {
+  const int e = gc / P, i = gc - e * P;
+  if (i != 0) {
+    ee[0] = e;
+    ii[0] = i;
+    return 1;
+  }
+  int n = 0;
+  if (e > 0) { ee[n] = e - 1; ii[n] = P; ++n; }
+  if (e < nel) { ee[n] = e; ii[n] = 0; ++n; }
+  return n;
+}
+
+// Sum over the elements sharing node g of evec[e][c][i] (fixed order).
+template <int DIM, int D>
+__device__ __forceinline__ double gather_node(const MeshDesc &m, const double *__restrict__ evec, int C,
+                                              int c, int g) {
+  constexpr int P = D - 1, ND = ipow<D, DIM>::value;
+  int ex[2], ix[2], ey[2], iy[2], ez[2] = {0, 0}, iz[2] = {0, 0};
+  const int gx = g % m.n1x;
+  const int t = g / m.n1x;
+  const int nxo = axis_owners(gx, P, m.nx, ex, ix);
+  int nyo, nzo = 1;
+  if constexpr (DIM == 2) {
+    nyo = axis_owners(t, P, m.ny, ey, iy);
+  } else {
+    nyo = axis_owners(t % m.n1y, P, m.ny, ey, iy);
+    nzo = axis_owners(t / m.n1y, P, m.nz, ez, iz);
+  }
+  double s = 0.0;
+  for (int a = 0; a < nzo; ++a)
+    for (int b = 0; b < nyo; ++b)
+      for (int k = 0; k < nxo; ++k) {
+        const int e = ex[k] + m.nx * (ey[b] + m.ny * ez[a]);
+        const int i = ix[k] + D * (iy[b] + D * iz[a]);
+        s += evec[((size_t)e * C + c) * ND + i];
+      }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Per-qpoint physics (reading of Sections 2.1 and 6):
+// EOS, tensor artificial viscosity, stress, force data and time-step bound.
+// ---------------------------------------------------------------------------
+constexpr double kEps0 = 1.0e-12;
+constexpr double kDegen = 1.0e-14;
+
+__device__ __forceinline__ double smooth_step01(double x, double e0) {
+  double y = (x + e0) / (2.0 * e0);
+  y = fmin(fmax(y, 0.0), 1.0);
+  return y * y * (3.0 - 2.0 * y);
+}
+
+// Smallest eigenvalue of a symmetric 2x2 (a b; b c) and, if s != nullptr, its unit eigenvector.
+__device__ __forceinline__ double eig_min2(double a, double b, double c, double *s) {
+  const double hd = 0.5 * (a - c);
+  const double lam = 0.5 * (a + c) - sqrt(hd * hd + b * b);
+  if (s) {
+    const double r0x = a - lam, r0y = b, r1x = b, r1y = c - lam;
+    const double n0 = sqrt(r0x * r0x + r0y * r0y), n1 = sqrt(r1x * r1x + r1y * r1y);
+    const bool first = n0 >= n1;
+    const double rx = first ? r0x : r1x, ry = first ? r0y : r1y, nr = first ? n0 : n1;
+    const double nA = sqrt(a * a + 2.0 * b * b + c * c);
+    if (nr <= kDegen * nA) {
+      s[0] = 1.0;
+      s[1] = 0.0;
+    } else {
+      s[0] = -ry / nr;
+      s[1] = rx / nr;
+    }
+  }
+  return lam;
+}
+
+// Smallest eigenvalue of a symmetric 3x3 (A[0..8], row-major, symmetric) by the
+// trigonometric closed form (Smith 1961) and, if s != nullptr, its unit eigenvector
+// from the largest cross product of two rows of (A - lam I).
+__device__ __forceinline__ double eig_min3(const double *A, double *s) {
+  const double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[4], a12 = A[5], a22 = A[8];
+  const double q = (a00 + a11 + a22) / 3.0;
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  const double d0 = a00 - q, d1 = a11 - q, d2 = a22 - q;
+  const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
+  const double pp = sqrt(p2 / 6.0);
+  double lam = q;
+  if (pp > 0.0) {
+    const double ip = 1.0 / pp;
+    const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
+    const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+    const double r = fmin(fmax(0.5 * detb, -1.0), 1.0);
+    const double phi = acos(r) / 3.0;
+    lam = q + 2.0 * pp * cos(phi + 2.0943951023931957);  // 2*pi/3
+  }
+  if (s) {
+    const double m00 = a00 - lam, m11 = a11 - lam, m22 = a22 - lam;
+    const double r0[3] = {m00, a01, a02}, r1[3] = {a01, m11, a12}, r2[3] = {a02, a12, m22};
+    double cr[3][3];
+    const double *ra[3] = {r0, r0, r1}, *rb[3] = {r1, r2, r2};
+    double nbest = -1.0;
+    int kbest = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cr[k][0] = ra[k][1] * rb[k][2] - ra[k][2] * rb[k][1];
+      cr[k][1] = ra[k][2] * rb[k][0] - ra[k][0] * rb[k][2];
+      cr[k][2] = ra[k][0] * rb[k][1] - ra[k][1] * rb[k][0];
+      const double n = sqrt(cr[k][0] * cr[k][0] + cr[k][1] * cr[k][1] + cr[k][2] * cr[k][2]);
+      if (n > nbest) { nbest = n; kbest = k; }
+    }
+    const double nM2 = m00 * m00 + m11 * m11 + m22 * m22 + 2.0 * (a01 * a01 + a02 * a02 + a12 * a12);
+    if (nbest <= kDegen * nM2) {
+      const double nM = sqrt(nM2);
+      const double nA = sqrt(a00 * a00 + a11 * a11 + a22 * a22 + 2.0 * p1);
+      if (nM <= kDegen * nA || nM == 0.0) {
+        s[0] = 1.0; s[1] = 0.0; s[2] = 0.0;
+      } else {
+        const double *rows[3] = {r0, r1, r2};
+        int rb_i = 0;
+        double rn = -1.0;
+        for (int k = 0; k < 3; ++k) {
+          const double n = sqrt(rows[k][0] * rows[k][0] + rows[k][1] * rows[k][1] + rows[k][2] * rows[k][2]);
+          if (n > rn) { rn = n; rb_i = k; }
+        }
+        const double *rv = rows[rb_i];
+        int kk = 0;
+        double amin = fabs(rv[0]);
+        if (fabs(rv[1]) < amin) { amin = fabs(rv[1]); kk = 1; }
+        if (fabs(rv[2]) < amin) { kk = 2; }
+        // rv x e_kk
+        double c0, c1, c2;
+        if (kk == 0) { c0 = 0.0; c1 = rv[2]; c2 = -rv[1]; }
+        else if (kk == 1) { c0 = -rv[2]; c1 = 0.0; c2 = rv[0]; }
+        else { c0 = rv[1]; c1 = -rv[0]; c2 = 0.0; }
+        const double n = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+        s[0] = c0 / n; s[1] = c1 / n; s[2] = c2 / n;
+      }
+    } else {
+      s[0] = cr[kbest][0] / nbest;
+      s[1] = cr[kbest][1] / nbest;
+      s[2] = cr[kbest][2] / nbest;
+    }
+  }
+  return lam;
+}
+
+struct QPointOut {
+  double inv_dt;   // 1/dt_q (before the CFL factor); +inf if inverted
+  bool inverted;
+};
+
+// J, Ji0, dV: row-major DIM x DIM. J[c][l] = dx_c/dxi_l, dV[c][l] = dv_c/dxi_l.
+// m = omega * rho0 * detJ0, w = omega, iw = 1/omega. Writes D[c*DIM+l].
+template <int DIM>
+__device__ __forceinline__ QPointOut qpoint_physics(const double *J, const double *Ji0, const double *dV, double e_q,
+                                                    double m, double w, double iw, const PhysParams &pp,
+                                                    bool want_dt, double *Dout) {
+  QPointOut o;
+  double Ji[DIM * DIM];
+  double det;
+  if constexpr (DIM == 2) {
+    det = J[0] * J[3] - J[1] * J[2];
+    const double id = 1.0 / det;
+    Ji[0] = J[3] * id; Ji[1] = -J[1] * id; Ji[2] = -J[2] * id; Ji[3] = J[0] * id;
+  } else {
+    const double c00 = J[4] * J[8] - J[5] * J[7];
+    const double c01 = J[5] * J[6] - J[3] * J[8];
+    const double c02 = J[3] * J[7] - J[4] * J[6];
+    det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+    const double id = 1.0 / det;
+    Ji[0] = c00 * id; Ji[1] = (J[2] * J[7] - J[1] * J[8]) * id; Ji[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+    Ji[3] = c01 * id; Ji[4] = (J[0] * J[8] - J[2] * J[6]) * id; Ji[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+    Ji[6] = c02 * id; Ji[7] = (J[1] * J[6] - J[0] * J[7]) * id; Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+  }
+  o.inverted = !(det > 0.0);
+  const double rho = m * iw / det;
+  const double ep = fmax(e_q, 0.0);
+  const double pres = (pp.gamma - 1.0) * rho * ep;
+  const double cs = sqrt(pp.gamma * (pp.gamma - 1.0) * ep);
+  // grad v = dV Jinv, strain = sym part
+  double gv[DIM * DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      double s = dV[c * DIM] * Ji[b];
+#pragma unroll
+      for (int l = 1; l < DIM; ++l) s = fma(dV[c * DIM + l], Ji[l * DIM + b], s);
+      gv[c * DIM + b] = s;
+    }
+  double eps[DIM * DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) eps[c * DIM + b] = 0.5 * (gv[c * DIM + b] + gv[b * DIM + c]);
+  double sigma[DIM * DIM];
+#pragma unroll
+  for (int k = 0; k < DIM * DIM; ++k) sigma[k] = 0.0;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) sigma[c * DIM + c] = -pres;
+  double mu = 0.0;
+  if (pp.use_viscosity) {
+    double s[DIM];
+    double lam;
+    if constexpr (DIM == 2) lam = eig_min2(eps[0], eps[1], eps[3], s);
+    else lam = eig_min3(eps, s);
+    // h = h0 |J Ji0 s|
+    double t[DIM], hv[DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) {
+      double a = Ji0[l * DIM] * s[0];
+#pragma unroll
+      for (int b = 1; b < DIM; ++b) a = fma(Ji0[l * DIM + b], s[b], a);
+      t[l] = a;
+    }
+    double hn2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      double a = J[c * DIM] * t[0];
+#pragma unroll
+      for (int l = 1; l < DIM; ++l) a = fma(J[c * DIM + l], t[l], a);
+      hv[c] = a;
+      hn2 = fma(a, a, hn2);
+    }
+    const double h = pp.h0 * sqrt(hn2);
+    mu = 2.0 * rho * h * h * fabs(lam) + 0.5 * rho * h * cs * (1.0 - smooth_step01(lam - 2.0 * kEps0, kEps0));
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) sigma[k] = fma(mu, eps[k], sigma[k]);
+  }
+  // D = w detJ sigma Jinv^T
+  const double wd = w * det;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c)
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) {
+      double a = sigma[c * DIM] * Ji[l * DIM];
+#pragma unroll
+      for (int b = 1; b < DIM; ++b) a = fma(sigma[c * DIM + b], Ji[l * DIM + b], a);
+      Dout[c * DIM + l] = wd * a;
+    }
+  o.inv_dt = 0.0;
+  if (want_dt) {
+    double lamJ;
+    if constexpr (DIM == 2) {
+      const double a = J[0] * J[0] + J[2] * J[2], b = J[0] * J[1] + J[2] * J[3], c = J[1] * J[1] + J[3] * J[3];
+      lamJ = eig_min2(a, b, c, nullptr);
+    } else {
+      double JtJ[9];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) JtJ[c * 3 + b] = J[c] * J[b] + J[3 + c] * J[3 + b] + J[6 + c] * J[6 + b];
+      lamJ = eig_min3(JtJ, nullptr);
+    }
+    const double hmin = sqrt(fmax(lamJ, 0.0)) / pp.order;
+    o.inv_dt = cs / hmin + 2.5 * mu / (rho * hmin * hmin);
+    if (o.inverted) o.inv_dt = INFINITY;
+  }
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// The kernel family for one (DIM, P, Q).
+// ---------------------------------------------------------------------------
+template <int DIM, int P, int Q>
+struct Family {
+  static constexpr int D = P + 1;
+  static constexpr int L = P;
+  static constexpr int ND = ipow<D, DIM>::value;
+  static constexpr int NL = ipow<L, DIM>::value;
+  static constexpr int NQ = ipow<Q, DIM>::value;
+  static constexpr int NB = NQ >= 128 ? 1 : (256 / NQ);   // elements per CTA
+  static constexpr int THREADS = ((NB * NQ < 256 ? NB * NQ : 256) + 31) / 32 * 32;
+  // basis table layout (doubles): B[Q][D] G[Q][D] Bt[D][Q] Gt[D][Q] Bl[Q][L] Blt[L][Q]
+  // B2t[D][Q] (squared B, transposed) w[Q] 1/w[Q] gll[D]
+  static constexpr int oB = 0, oG = Q * D, oBt = 2 * Q * D, oGt = 3 * Q * D, oBl = 4 * Q * D,
+                       oBlt = 4 * Q * D + Q * L, oB2t = 4 * Q * D + 2 * Q * L, oW = 5 * Q * D + 2 * Q * L,
+                       oIW = oW + Q, oZ = oIW + Q;
+  static constexpr int TAB = ((oZ + D) + 1) / 2 * 2;
+  static constexpr int RED = 4 * 32;   // reduction scratch
+
+  static constexpr int CX = NB * DIM;        // one H1 vector field of NB elements
+  static constexpr int C2X = NB * 2 * DIM;   // two H1 vector fields
+  static constexpr int max3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
+
+  static __device__ __forceinline__ void load_tab(double *s, const double *__restrict__ tab) {
+    for (int k = threadIdx.x; k < oZ + D; k += blockDim.x) s[k] = tab[k];
+  }
+  static __device__ __forceinline__ void qweight(const double *st, int q, double &w, double &iw) {
+    const int qx = q % Q;
+    if constexpr (DIM == 2) {
+      const int qy = q / Q;
+      w = st[oW + qx] * st[oW + qy];
+      iw = st[oIW + qx] * st[oIW + qy];
+    } else {
+      const int qy = (q / Q) % Q, qz = q / (Q * Q);
+      w = st[oW + qx] * st[oW + qy] * st[oW + qz];
+      iw = st[oIW + qx] * st[oIW + qy] * st[oIW + qz];
+    }
+  }
+  // gather C_ = NB*ncomp components of an H1 vector field into u[b*ncomp + c][i]
+  static __device__ __forceinline__ void gather_elem(double *u, const double *__restrict__ f, int ncomp,
+                                                     const MeshDesc &m, int e0, int nb) {
+    for (int k = threadIdx.x; k < NB * ncomp * ND; k += blockDim.x) {
+      const int i = k % ND, bc = k / ND, c = bc % ncomp, b = bc / ncomp;
+      u[k] = b < nb ? f[(size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i)] : 0.0;
+    }
+  }
+  static __device__ __forceinline__ void apply_me_inv(const double *__restrict__ me_inv, const double *rhs, int e,
+                                                      int j, double &s) {
+    const double *Mi = me_inv + ((size_t)e * NL + j) * NL;
+    s = Mi[0] * rhs[0];
+    for (int kk = 1; kk < NL; ++kk) s = fma(Mi[kk], rhs[kk], s);
+  }
+
+  // ===== quadrature data (rows a1-a7) =====================================
+  // smem: tab | u[C2X][ND] | S (grad scratch C2X) | g[DIM][C2X][NQ] | eq[NB][NQ] | el[NB][NL] | red
+  static constexpr int QD_S = max3(grad_scratch<DIM, D, Q>(C2X), interp_scratch<DIM, L, Q>(NB), 0);
+  static constexpr size_t qdata_smem() {
+    return sizeof(double) * (TAB + C2X * ND + QD_S + DIM * C2X * NQ + NB * NQ + NB * NL + RED);
+  }
+  static __device__ __forceinline__ void body_qdata(QdataArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *S = u + C2X * ND, *g = S + QD_S, *eq = g + DIM * C2X * NQ;
+    double *el = eq + NB * NQ, *red = el + NB * NL;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    for (int k = threadIdx.x; k < C2X * ND; k += blockDim.x) {
+      const int i = k % ND, bc = k / ND, c = bc % (2 * DIM), b = bc / (2 * DIM);
+      double val = 0.0;
+      if (b < nb) {
+        const int gi = h1_node<DIM, D>(m, e0 + b, i);
+        val = c < DIM ? a.x[(size_t)c * m.nh1 + gi] : a.v[(size_t)(c - DIM) * m.nh1 + gi];
+      }
+      u[k] = val;
+    }
+    for (int k = threadIdx.x; k < NB * NL; k += blockDim.x)
+      el[k] = k / NL < nb ? a.e[(size_t)e0 * NL + k] : 0.0;
+    __syncthreads();
+    interp<DIM, L, Q, NB>(el, eq, S, st + oBl);   // energy at qpoints
+    grad_ref<DIM, D, Q, C2X>(u, g, S, st + oB, st + oG);
+    double inv_dt_max = 0.0;
+    for (int k = threadIdx.x; k < nb * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      const size_t e = (size_t)(e0 + b);
+      double J[DIM * DIM], dV[DIM * DIM], Ji0[DIM * DIM], Dq[DIM * DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) {
+          J[c * DIM + l] = g[(l * C2X + b * 2 * DIM + c) * NQ + q];
+          dV[c * DIM + l] = g[(l * C2X + b * 2 * DIM + DIM + c) * NQ + q];
+        }
+#pragma unroll
+      for (int r = 0; r < DIM * DIM; ++r) Ji0[r] = a.jinv0[(e * DIM * DIM + r) * NQ + q];
+      double w, iw;
+      qweight(st, q, w, iw);
+      const QPointOut o = qpoint_physics<DIM>(J, Ji0, dV, eq[k], a.mq[e * NQ + q], w, iw, a.phys, a.want_dt, Dq);
+      if (o.inverted) latch_status(a.status, 4);
+#pragma unroll
+      for (int r = 0; r < DIM * DIM; ++r) a.D[(e * DIM * DIM + r) * NQ + q] = Dq[r];
+      inv_dt_max = fmax(inv_dt_max, o.inv_dt);
+    }
+    if (!a.want_dt) return;
+    // grid max of 1/dt: per-block partial; the last block to finish reduces (fixed order).
+    const double bm = block_max(inv_dt_max, red);
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      a.partials[blockIdx.x] = bm;
+      __threadfence();
+      s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) mx = fmax(mx, ((volatile double *)a.partials)[i]);
+    mx = warp_max(mx);
+    if (threadIdx.x == 0) {
+      *a.counter = 0u;
+      const double dt_est = mx > 0.0 ? a.cfl / mx : (mx == 0.0 ? INFINITY : 0.0);
+      if (a.dt_est_out) *a.dt_est_out = dt_est;
+      if (a.step) {
+        a.step->dt_est = dt_est;
+        double dt = a.fixed_dt;
+        if (!(dt > 0.0)) dt = fmin(dt_est, a.step->t_end - a.step->t);
+        if (!(dt > 0.0)) dt = 0.0;
+        a.step->dt = dt;
+      }
+    }
+  }
+
+  // ===== force product F.u (row b1), element part -> E-vector =============
+  // smem: tab | f[DIM][CX][NQ] | S | y[CX][ND] | ul[NB][NL] | uq[NB][NQ]
+  static constexpr int F_S = max3(grad_scratch<DIM, D, Q>(CX), interp_scratch<DIM, L, Q>(NB), 0);
+  static constexpr size_t force_smem() {
+    return sizeof(double) * (TAB + DIM * CX * NQ + F_S + CX * ND + NB * NL + NB * NQ);
+  }
+  static __device__ __forceinline__ void body_force(ForceArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *f = st + TAB, *S = f + DIM * CX * NQ, *y = S + F_S, *ul = y + CX * ND, *uq = ul + NB * NL;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    // D[e][c*DIM+l][q] -> f[l][b*DIM+c][q]  (one contiguous global block per CTA)
+    for (int k = threadIdx.x; k < NB * DIM * DIM * NQ; k += blockDim.x) {
+      const int q = k % NQ, r = (k / NQ) % (DIM * DIM), b = k / (NQ * DIM * DIM);
+      const int c = r / DIM, l = r % DIM;
+      f[(l * CX + b * DIM + c) * NQ + q] = b < nb ? a.D[(size_t)e0 * DIM * DIM * NQ + k] : 0.0;
+    }
+    if (a.u) {
+      for (int k = threadIdx.x; k < NB * NL; k += blockDim.x)
+        ul[k] = k / NL < nb ? a.u[(size_t)e0 * NL + k] : 0.0;
+      __syncthreads();
+      interp<DIM, L, Q, NB>(ul, uq, S, st + oBl);
+      for (int k = threadIdx.x; k < DIM * CX * NQ; k += blockDim.x) {
+        const int q = k % NQ, b = ((k / NQ) % CX) / DIM;
+        f[k] *= uq[b * NQ + q];
+      }
+    }
+    __syncthreads();
+    grad_ref_t<DIM, D, Q, CX>(f, y, S, st + oBt, st + oGt);
+    for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = y[k];
+  }
+
+  // ===== transposed force product F^T v (row b2), optionally fused with the
+  // TG-2D energy source, the energy solve M_E^{-1} (row c3) and the e update (row c4).
+  // smem: tab | u[CX][ND] | xu[CX][ND] | S | g[DIM][CX][NQ] | xq[CX][NQ] | sq[NB][NQ] | out[NB][NL] | red
+  static constexpr int FT_S = max3(grad_scratch<DIM, D, Q>(CX), interp_scratch<DIM, D, Q>(CX),
+                                   interp_scratch<DIM, Q, L>(NB));
+  static constexpr size_t force_t_smem() {
+    return sizeof(double) * (TAB + 2 * CX * ND + FT_S + DIM * CX * NQ + CX * NQ + NB * NQ + NB * NL + RED);
+  }
+  static __device__ __forceinline__ void body_force_t(ForceTArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *xu = u + CX * ND, *S = xu + CX * ND, *g = S + FT_S;
+    double *xq = g + DIM * CX * NQ, *sq = xq + CX * NQ, *out = sq + NB * NQ, *red = out + NB * NL;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(u, a.v, DIM, m, e0, nb);
+    if (a.src_x) gather_elem(xu, a.src_x, DIM, m, e0, nb);
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(u, g, S, st + oB, st + oG);
+    if (a.src_x) interp<DIM, D, Q, CX>(xu, xq, S, st + oB);   // positions at qpoints
+    double src_sum = 0.0;
+    for (int k = threadIdx.x; k < NB * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      double s = 0.0;
+      if (b < nb) {
+        const size_t base = (size_t)(e0 + b) * DIM * DIM * NQ + q;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int l = 0; l < DIM; ++l)
+            s = fma(a.D[base + (size_t)(c * DIM + l) * NQ], g[(l * CX + b * DIM + c) * NQ + q], s);
+        if (a.src_x) {
+          // 2D Taylor-Green internal-energy source Q(x), weighted by omega rho0 detJ0
+          const double X = xq[(b * DIM + 0) * NQ + q], Y = xq[(b * DIM + 1) * NQ + q];
+          const double pi = 3.141592653589793;
+          const double Qs = (3.0 * pi / 8.0) * (cos(3.0 * pi * X) * cos(pi * Y) - cos(pi * X) * cos(3.0 * pi * Y));
+          const double sv = a.mq[(size_t)(e0 + b) * NQ + q] * Qs;
+          s += sv;
+          src_sum += sv;
+        }
+      }
+      sq[k] = s;
+    }
+    __syncthreads();
+    interp<DIM, Q, L, NB>(sq, out, S, st + oBlt);   // sum_q phi_j(q) s_q
+    if (!a.me_inv) {
+      for (int k = threadIdx.x; k < nb * NL; k += blockDim.x) a.out[(size_t)e0 * NL + k] = out[k];
+    } else {
+      const double coef = a.coef * *a.dt;
+      for (int k = threadIdx.x; k < nb * NL; k += blockDim.x) {
+        const int b = k / NL, j = k % NL;
+        double s;
+        apply_me_inv(a.me_inv, out + b * NL, e0 + b, j, s);
+        const size_t idx = (size_t)e0 * NL + k;
+        a.out[idx] = fma(coef, s, a.e_base[idx]);
+      }
+    }
+    if (!a.src_sum) return;
+    double v1[1] = {src_sum};
+    block_sum<1>(v1, red);
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      a.partials[blockIdx.x] = v1[0];
+      __threadfence();
+      s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double sacc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) sacc += ((volatile double *)a.partials)[i];
+    sacc = warp_sum(sacc);
+    if (threadIdx.x == 0) {
+      *a.counter = 0u;
+      *a.src_sum = sacc * *a.dt;
+    }
+  }
+
+  // ===== PA mass action (row c1), element part =============================
+  // smem: tab | u[CX][ND] | S | uq[CX][NQ] | y[CX][ND] | red
+  static constexpr int M_S = max3(interp_scratch<DIM, D, Q>(CX), interp_scratch<DIM, Q, D>(CX), 0);
+  static constexpr size_t mass_smem() {
+    return sizeof(double) * (TAB + CX * ND + M_S + CX * NQ + CX * ND + RED);
+  }
+  // y_e = B^T diag(mq) B u_e for the DIM components of NB elements
+  static __device__ __forceinline__ void mass_elem(const double *st, const double *u, double *S, double *uq,
+                                                   double *y, const double *__restrict__ mq, int e0, int nb) {
+    interp<DIM, D, Q, CX>(u, uq, S, st + oB);
+    for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
+      const int q = k % NQ, b = (k / NQ) / DIM;
+      uq[k] *= b < nb ? mq[(size_t)(e0 + b) * NQ + q] : 0.0;
+    }
+    __syncthreads();
+    interp<DIM, Q, D, CX>(uq, y, S, st + oBt);
+  }
+  static __device__ __forceinline__ void body_mass(MassArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *S = u + CX * ND, *uq = S + M_S, *y = uq + CX * NQ;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(u, a.x, DIM, m, e0, nb);
+    __syncthreads();
+    mass_elem(st, u, S, uq, y, a.mq, e0, nb);
+    for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = y[k];
+  }
+
+  // ===== Jacobi-PCG on the PA mass operator (row c2), one persistent launch
+  static constexpr size_t cg_smem() { return mass_smem(); }
+  static __device__ __forceinline__ void body_cg(CgArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *S = u + CX * ND, *uq = S + M_S, *y = uq + CX * NQ, *red = y + CX * ND;
+    __shared__ double s_sc[4];
+    const MeshDesc &m = a.mesh;
+    const int nbatch = (m.ne + NB - 1) / NB;
+    const int G = gridDim.x;
+    const size_t nv = (size_t)DIM * m.nh1;
+    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gstride = (size_t)G * blockDim.x;
+    load_tab(st, a.tab);
+    __syncthreads();
+
+    // Phase A: E-vector of M applied to (mode 0) the masked initial guess x or
+    // (mode 1) the new search direction p_new = invdiag*r + beta*p_old.
+    auto phase_a = [&](int mode, double beta) {
+      for (int bt = blockIdx.x; bt < nbatch; bt += G) {
+        const int e0 = bt * NB;
+        const int nb = min(NB, m.ne - e0);
+        for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+          const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+          double val = 0.0;
+          if (b < nb) {
+            const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
+            const double idg = a.invdiag[gi];
+            if (mode == 0) val = idg != 0.0 ? a.x[gi] : 0.0;
+            else val = fma(beta, a.p[gi], idg * a.r[gi]);
+          }
+          u[k] = val;
+        }
+        __syncthreads();
+        mass_elem(st, u, S, uq, y, a.mq, e0, nb);
+        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = y[k];
+        __syncthreads();
+      }
+    };
+    auto finish = [&](int iters, int status, double rr, double bb) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double bn = sqrt(bb);
+        const double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+        if (a.info) {
+          a.info->iters = iters;
+          a.info->status = status;
+          a.info->rel_res = rel;
+          a.info->b_norm = bn;
+        }
+        if (a.iters_out) *a.iters_out = iters;
+        if (a.relres_out) *a.relres_out = rel;
+        if (status) latch_status(a.status, status);
+      }
+    };
+
+    // ---- init: r = b - A x0 on free DOFs, p = z = invdiag r
+    phase_a(0, 0.0);
+    if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(0, kStatusTimeout, 0.0, 0.0); return; }
+    {
+      double acc[3] = {0.0, 0.0, 0.0};  // b.b, r.r, r.z
+      for (size_t k = gtid; k < nv; k += gstride) {
+        const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
+        const double idg = a.invdiag[k];
+        double rv = 0.0;
+        if (idg != 0.0) {
+          const double bv = a.b[k];
+          rv = bv - gather_node<DIM, D>(m, a.evec, DIM, c, gn);
+          acc[0] = fma(bv, bv, acc[0]);
+          acc[1] = fma(rv, rv, acc[1]);
+          acc[2] = fma(rv * idg, rv, acc[2]);
+        } else {
+          a.x[k] = 0.0;
+        }
+        a.r[k] = rv;
+        a.p[k] = idg * rv;
+      }
+      block_sum<3>(acc, red);
+      if (threadIdx.x == 0) {
+        a.partials[0 * G + blockIdx.x] = acc[0];
+        a.partials[1 * G + blockIdx.x] = acc[1];
+        a.partials[2 * G + blockIdx.x] = acc[2];
+      }
+    }
+    if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(0, kStatusTimeout, 0.0, 0.0); return; }
+    if (threadIdx.x < 32) {
+      const double s0 = warp_sum_partials(a.partials, G);
+      const double s1 = warp_sum_partials(a.partials + (size_t)G, G);
+      const double s2 = warp_sum_partials(a.partials + 2 * (size_t)G, G);
+      if (threadIdx.x == 0) { s_sc[0] = s0; s_sc[1] = s1; s_sc[2] = s2; }
+    }
+    __syncthreads();
+    const double bb = s_sc[0];
+    double rr = s_sc[1], rz = s_sc[2], rz_old = rz;
+    const double tol2 = a.tol * a.tol * bb;
+    if (bb == 0.0) {
+      for (size_t k = gtid; k < nv; k += gstride) a.x[k] = 0.0;
+      finish(0, 0, 0.0, 0.0);
+      return;
+    }
+    int it = 0;
+    for (;;) {
+      if (rr <= tol2) { finish(it, 0, rr, bb); return; }
+      if (it >= a.max_it) { finish(it, 5, rr, bb); return; }
+      const double beta = it == 0 ? 0.0 : rz / rz_old;
+      rz_old = rz;
+      phase_a(1, beta);
+      if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(it, kStatusTimeout, rr, bb); return; }
+      {  // Phase B: Ap, p_new, p.Ap
+        double acc[1] = {0.0};
+        for (size_t k = gtid; k < nv; k += gstride) {
+          const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
+          const double idg = a.invdiag[k];
+          double ap = 0.0, pn = 0.0;
+          if (idg != 0.0) {
+            ap = gather_node<DIM, D>(m, a.evec, DIM, c, gn);
+            pn = fma(beta, a.p[k], idg * a.r[k]);
+            acc[0] = fma(pn, ap, acc[0]);
+          }
+          a.ap[k] = ap;
+          a.p[k] = pn;
+        }
+        block_sum<1>(acc, red);
+        if (threadIdx.x == 0) a.partials[3 * G + blockIdx.x] = acc[0];
+      }
+      if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(it, kStatusTimeout, rr, bb); return; }
+      if (threadIdx.x < 32) {
+        const double s = warp_sum_partials(a.partials + 3 * (size_t)G, G);
+        if (threadIdx.x == 0) s_sc[3] = s;
+      }
+      __syncthreads();
+      const double alpha = rz / s_sc[3];
+      {  // Phase C: x += alpha p, r -= alpha Ap, new r.r and r.z
+        double acc[2] = {0.0, 0.0};
+        for (size_t k = gtid; k < nv; k += gstride) {
+          const double idg = a.invdiag[k];
+          if (idg != 0.0) {
+            a.x[k] = fma(alpha, a.p[k], a.x[k]);
+            const double rv = fma(-alpha, a.ap[k], a.r[k]);
+            a.r[k] = rv;
+            acc[0] = fma(rv, rv, acc[0]);
+            acc[1] = fma(rv * idg, rv, acc[1]);
+          }
+        }
+        block_sum<2>(acc, red);
+        if (threadIdx.x == 0) {
+          a.partials[1 * G + blockIdx.x] = acc[0];
+          a.partials[2 * G + blockIdx.x] = acc[1];
+        }
+      }
+      if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(it, kStatusTimeout, rr, bb); return; }
+      if (threadIdx.x < 32) {
+        const double s1 = warp_sum_partials(a.partials + 1 * (size_t)G, G);
+        const double s2 = warp_sum_partials(a.partials + 2 * (size_t)G, G);
+        if (threadIdx.x == 0) { s_sc[1] = s1; s_sc[2] = s2; }
+      }
+      __syncthreads();
+      rr = s_sc[1];
+      rz = s_sc[2];
+      ++it;
+    }
+  }
+
+  // ===== setup: geometry at qpoints (J0, detJ0, J0^{-1}, mass data) =======
+  // smem: tab | u[CX][ND] | S | g[DIM][CX][NQ] | red
+  static constexpr int GE_S = grad_scratch<DIM, D, Q>(CX);
+  static constexpr size_t geom_smem() { return sizeof(double) * (TAB + CX * ND + GE_S + DIM * CX * NQ + RED); }
+  static __device__ __forceinline__ void body_geom(GeomArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *S = u + CX * ND, *g = S + GE_S, *red = g + DIM * CX * NQ;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(u, a.x0, DIM, m, e0, nb);
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(u, g, S, st + oB, st + oG);
+    double vol = 0.0;
+    for (int k = threadIdx.x; k < nb * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      const size_t e = e0 + b;
+      double J[DIM * DIM], Ji[DIM * DIM], det;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) J[c * DIM + l] = g[(l * CX + b * DIM + c) * NQ + q];
+      if constexpr (DIM == 2) {
+        det = J[0] * J[3] - J[1] * J[2];
+        Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
+      } else {
+        const double c00 = J[4] * J[8] - J[5] * J[7];
+        const double c01 = J[5] * J[6] - J[3] * J[8];
+        const double c02 = J[3] * J[7] - J[4] * J[6];
+        det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+        Ji[0] = c00 / det; Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det; Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+        Ji[3] = c01 / det; Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det; Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+        Ji[6] = c02 / det; Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det; Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+      }
+      if (!(det > 0.0)) latch_status(a.status, 4);
+      double w, iw;
+      qweight(st, q, w, iw);
+      const double rho0 = a.rho0_in ? a.rho0_in[e * NQ + q] : 1.0;
+      a.rho0[e * NQ + q] = rho0;
+      a.mq[e * NQ + q] = w * rho0 * det;
+#pragma unroll
+      for (int r = 0; r < DIM * DIM; ++r) a.jinv0[(e * DIM * DIM + r) * NQ + q] = Ji[r];
+      vol = fma(w, det, vol);
+    }
+    double v1[1] = {vol};
+    block_sum<1>(v1, red);
+    if (threadIdx.x == 0) a.partials[blockIdx.x] = v1[0];
+  }
+
+  // ===== setup: per-element diagonal of M (sum_q mq B_i(q)^2) ==============
+  static constexpr int DG_S = interp_scratch<DIM, Q, D>(NB);
+  static constexpr size_t diag_smem() { return sizeof(double) * (TAB + NB * NQ + DG_S + NB * ND); }
+  static __device__ __forceinline__ void body_diag(DiagArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *mq = st + TAB, *S = mq + NB * NQ, *y = S + DG_S;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    for (int k = threadIdx.x; k < NB * NQ; k += blockDim.x) mq[k] = k / NQ < nb ? a.mq[(size_t)e0 * NQ + k] : 0.0;
+    __syncthreads();
+    interp<DIM, Q, D, NB>(mq, y, S, st + oB2t);
+    for (int k = threadIdx.x; k < nb * ND; k += blockDim.x) a.evec[(size_t)e0 * ND + k] = y[k];
+  }
+
+  // ===== setup: element energy-mass inverses (Gauss-Jordan on SPD) ========
+  static constexpr size_t emass_smem() { return sizeof(double) * (TAB + NQ + 2 * NL * NL + NL); }
+  static __device__ __forceinline__ void body_emass(EmassArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *mq = st + TAB, *A = mq + NQ, *Inv = A + NL * NL, *col = Inv + NL * NL;
+    const size_t e = blockIdx.x;
+    load_tab(st, a.tab);
+    for (int k = threadIdx.x; k < NQ; k += blockDim.x) mq[k] = a.mq[e * NQ + k];
+    __syncthreads();
+    for (int k = threadIdx.x; k < NL * NL; k += blockDim.x) {   // A_jk = sum_q mq phi_j phi_k
+      const int j = k / NL, kk = k % NL;
+      double s = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        const int qx = q % Q, jx = j % L, kx = kk % L;
+        double pj = st[oBl + qx * L + jx], pk = st[oBl + qx * L + kx];
+        if constexpr (DIM == 2) {
+          const int qy = q / Q, jy = j / L, ky = kk / L;
+          pj *= st[oBl + qy * L + jy];
+          pk *= st[oBl + qy * L + ky];
+        } else {
+          const int qy = (q / Q) % Q, jy = (j / L) % L, ky = (kk / L) % L;
+          const int qz = q / (Q * Q), jz = j / (L * L), kz = kk / (L * L);
+          pj *= st[oBl + qy * L + jy] * st[oBl + qz * L + jz];
+          pk *= st[oBl + qy * L + ky] * st[oBl + qz * L + kz];
+        }
+        s = fma(mq[q] * pj, pk, s);
+      }
+      A[k] = s;
+      Inv[k] = (j == kk) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int piv = 0; piv < NL; ++piv) {
+      const double d = A[piv * NL + piv];
+      for (int k = threadIdx.x; k < NL; k += blockDim.x) col[k] = A[k * NL + piv];
+      __syncthreads();
+      for (int k = threadIdx.x; k < NL; k += blockDim.x) {
+        A[piv * NL + k] /= d;
+        Inv[piv * NL + k] /= d;
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < NL * NL; k += blockDim.x) {
+        const int i = k / NL, j = k % NL;
+        if (i == piv) continue;
+        const double f = col[i];
+        A[k] = fma(-f, A[piv * NL + j], A[k]);
+        Inv[k] = fma(-f, Inv[piv * NL + j], Inv[k]);
+      }
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < NL * NL; k += blockDim.x) a.me_inv[e * NL * NL + k] = Inv[k];
+  }
+
+  // ===== initial energy: element L2 projection of p0/((gamma-1) rho0) =====
+  // smem: tab | u[CX][ND] | S | xq[CX][NQ] | sq[NB][NQ] | rhs[NB][NL]
+  static constexpr int IE_S = max3(interp_scratch<DIM, D, Q>(CX), interp_scratch<DIM, Q, L>(NB), 0);
+  static constexpr size_t init_e_smem() {
+    return sizeof(double) * (TAB + CX * ND + IE_S + CX * NQ + NB * NQ + NB * NL);
+  }
+  static __device__ __forceinline__ void body_init_e(InitEArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *S = u + CX * ND, *xq = S + IE_S, *sq = xq + CX * NQ, *rhs = sq + NB * NQ;
+    const MeshDesc &m = a.mesh;
+    const int e0 = blockIdx.x * NB;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(u, a.x0, DIM, m, e0, nb);
+    __syncthreads();
+    interp<DIM, D, Q, CX>(u, xq, S, st + oB);
+    const double pi = 3.141592653589793;
+    for (int k = threadIdx.x; k < NB * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      double val = 0.0;
+      if (b < nb) {
+        const size_t eq = (size_t)(e0 + b) * NQ + q;
+        const double X = xq[(b * DIM + 0) * NQ + q], Y = xq[(b * DIM + 1) * NQ + q];
+        const double Z = DIM == 3 ? xq[(b * DIM + DIM - 1) * NQ + q] : 0.0;
+        const double rho0 = a.rho0[eq];
+        double pr;
+        if (a.problem == 0) {
+          if (DIM == 2) pr = 0.25 * rho0 * (cos(2 * pi * X) + cos(2 * pi * Y)) + 1.0;
+          else pr = 100.0 + rho0 / 16.0 * (cos(2 * pi * X) + cos(2 * pi * Y)) * (cos(2 * pi * Z) + 2.0);
+        } else {
+          const double r = sqrt(X * X + Y * Y);
+          if (r < 0.2) pr = 5.0 + 12.5 * r * r;
+          else if (r < 0.4) pr = 9.0 - 4.0 * log(0.2) + 12.5 * r * r - 20.0 * r + 4.0 * log(r);
+          else pr = 3.0 + 4.0 * log(2.0);
+        }
+        val = a.mq[eq] * pr / ((a.gamma - 1.0) * rho0);
+      }
+      sq[k] = val;
+    }
+    __syncthreads();
+    interp<DIM, Q, L, NB>(sq, rhs, S, st + oBlt);
+    for (int k = threadIdx.x; k < nb * NL; k += blockDim.x) {
+      const int b = k / NL, j = k % NL;
+      double s;
+      apply_me_inv(a.me_inv, rhs + b * NL, e0 + b, j, s);
+      a.e[(size_t)e0 * NL + k] = s;
+    }
+  }
+};
+
+// Kernel entry points (free templates; the bodies live in Family).
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_qdata(QdataArgs a) { Family<DIM, P, Q>::body_qdata(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force(ForceArgs a) { Family<DIM, P, Q>::body_force(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force_t(ForceTArgs a) { Family<DIM, P, Q>::body_force_t(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_mass(MassArgs a) { Family<DIM, P, Q>::body_mass(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_cg(CgArgs a) { Family<DIM, P, Q>::body_cg(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_geom(GeomArgs a) { Family<DIM, P, Q>::body_geom(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_diag(DiagArgs a) { Family<DIM, P, Q>::body_diag(a); }
+template <int DIM, int P, int Q>
+__global__ void k_emass(EmassArgs a) { Family<DIM, P, Q>::body_emass(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_init_e(InitEArgs a) { Family<DIM, P, Q>::body_init_e(a); }
+
+}  // namespace lh

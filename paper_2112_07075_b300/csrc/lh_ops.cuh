@@ -1,0 +1,67 @@
+// Builds the launcher table (Ops) of one compiled (DIM, P, Q) kernel family.
+#pragma once
+
+#include "lh_kernels.cuh"
+
+namespace lh {
+
+template <int DIM, int D>
+__global__ void k_gather(MeshDesc m, const double *__restrict__ evec, int C, double *__restrict__ out, double scale,
+                         const double *__restrict__ mask) {
+  const size_t n = (size_t)C * m.nh1;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k / m.nh1), g = (int)(k % m.nh1);
+    double v = scale * gather_node<DIM, D>(m, evec, C, c, g);
+    if (mask && mask[k] == 0.0) v = 0.0;
+    out[k] = v;
+  }
+}
+
+template <int DIM, int P, int Q>
+struct OpsBuilder {
+  using F = Family<DIM, P, Q>;
+  static void qdata(const QdataArgs &a, int grid, cudaStream_t s) {
+    k_qdata<DIM, P, Q><<<grid, F::THREADS, F::qdata_smem(), s>>>(a);
+  }
+  static void force(const ForceArgs &a, int grid, cudaStream_t s) {
+    k_force<DIM, P, Q><<<grid, F::THREADS, F::force_smem(), s>>>(a);
+  }
+  static void force_t(const ForceTArgs &a, int grid, cudaStream_t s) {
+    k_force_t<DIM, P, Q><<<grid, F::THREADS, F::force_t_smem(), s>>>(a);
+  }
+  static void mass(const MassArgs &a, int grid, cudaStream_t s) {
+    k_mass<DIM, P, Q><<<grid, F::THREADS, F::mass_smem(), s>>>(a);
+  }
+  static cudaError_t cg(CgArgs &a, int grid, cudaStream_t s) {
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)k_cg<DIM, P, Q>, dim3(grid), dim3(F::THREADS), args, F::cg_smem(), s);
+  }
+  static void geom(const GeomArgs &a, int grid, cudaStream_t s) {
+    k_geom<DIM, P, Q><<<grid, F::THREADS, F::geom_smem(), s>>>(a);
+  }
+  static void diag(const DiagArgs &a, int grid, cudaStream_t s) {
+    k_diag<DIM, P, Q><<<grid, F::THREADS, F::diag_smem(), s>>>(a);
+  }
+  static void emass(const EmassArgs &a, int grid, cudaStream_t s) {
+    k_emass<DIM, P, Q><<<grid, 128, F::emass_smem(), s>>>(a);
+  }
+  static void init_e(const InitEArgs &a, int grid, cudaStream_t s) {
+    k_init_e<DIM, P, Q><<<grid, F::THREADS, F::init_e_smem(), s>>>(a);
+  }
+  static void gather(const MeshDesc &m, const double *evec, int C, double *out, double scale, const double *mask,
+                     int grid, int threads, cudaStream_t s) {
+    k_gather<DIM, P + 1><<<grid, threads, 0, s>>>(m, evec, C, out, scale, mask);
+  }
+  static const Ops *get() {
+    static const Ops ops = {DIM, P, Q, F::NB, F::THREADS,
+                            F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
+                            F::geom_smem(), F::diag_smem(), F::emass_smem(), F::init_e_smem(),
+                            (void *)k_qdata<DIM, P, Q>, (void *)k_force<DIM, P, Q>, (void *)k_force_t<DIM, P, Q>, (void *)k_mass<DIM, P, Q>,
+                            (void *)k_cg<DIM, P, Q>, (void *)k_geom<DIM, P, Q>, (void *)k_diag<DIM, P, Q>, (void *)k_emass<DIM, P, Q>,
+                            (void *)k_init_e<DIM, P, Q>,
+                            &qdata, &force, &force_t, &mass, &cg, &geom, &diag, &emass, &init_e, &gather};
+    return &ops;
+  }
+};
+
+}  // namespace lh

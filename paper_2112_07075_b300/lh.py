@@ -1,0 +1,224 @@
+"""Thin ctypes binding of liblh.so (include/lh.h) with the same names.
+
+Argument marshalling only: device buffers are torch CUDA tensors whose raw
+pointers are passed to the library; every step of the hot path runs in the
+library's CUDA kernels. The library is loaded from this package directory; if it
+is missing the import fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblh.so")
+
+LH_OK, LH_ERR_ARG, LH_ERR_CUDA, LH_ERR_OOM, LH_ERR_INVERTED, LH_ERR_NOT_CONVERGED, LH_ERR_TIMEOUT, \
+    LH_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["ok", "argument", "cuda", "out of memory", "inverted", "not converged", "timeout", "unsupported"]
+PROBLEMS = {"taylor_green": 0, "gresho": 1}
+SOURCES = {"none": 0, "tg2d": 1}
+PRECISIONS = {"fp64": 0, "fp32_ir": 1}
+
+EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_status", "lh_init_state",
+            "lh_update_qdata", "lh_copy_qdata", "lh_force_mult", "lh_force_mult_t", "lh_mass_mult",
+            "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step"]
+
+
+class LhParams(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("vertices", ctypes.POINTER(ctypes.c_double)), ("order", ctypes.c_int), ("q1", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("use_viscosity", ctypes.c_int),
+                ("source", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class LhSizes(ctypes.Structure):
+    _fields_ = [("ne", ctypes.c_int64), ("n_h1", ctypes.c_int64), ("nv", ctypes.c_int64),
+                ("n_l2", ctypes.c_int64), ("nq", ctypes.c_int64), ("arena_bytes", ctypes.c_int64)]
+
+
+class LhCgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("b_norm", ctypes.c_double)]
+
+
+class LhStepInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("t_end", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dt_est", ctypes.c_double), ("energy_src", ctypes.c_double),
+                ("cg_rel_res", ctypes.c_double * 2), ("cg_iters", ctypes.c_int * 2),
+                ("status", ctypes.c_int), ("steps", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblh.so (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblh.so not found at {path}; build it with python -m paper_2112_07075_b300.build")
+    lib = ctypes.CDLL(path)
+    P, I, D, VP = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "lh_setup": (I, [ctypes.POINTER(LhParams), P, ctypes.POINTER(P)]),
+        "lh_destroy": (None, [P]),
+        "lh_get_sizes": (I, [P, ctypes.POINTER(LhSizes)]),
+        "lh_last_error": (ctypes.c_char_p, [P]),
+        "lh_sync_status": (I, [P]),
+        "lh_init_state": (I, [P, I, VP, VP, VP, VP]),
+        "lh_update_qdata": (I, [P, VP, VP, VP, VP, VP]),
+        "lh_copy_qdata": (I, [P, VP, VP]),
+        "lh_force_mult": (I, [P, VP, VP, VP]),
+        "lh_force_mult_t": (I, [P, VP, VP, VP]),
+        "lh_mass_mult": (I, [P, VP, VP, VP]),
+        "lh_mass_cg": (I, [P, VP, VP, D, I, VP, VP]),
+        "lh_energy_solve": (I, [P, VP, VP, VP]),
+        "lh_rk2avg_step": (I, [P, VP, VP, VP, D, D, I, VP, VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Sizes:
+    ne: int
+    n_h1: int
+    nv: int
+    n_l2: int
+    nq: int
+    arena_bytes: int
+
+
+class Context:
+    """One problem instance: owns an lh_ctx (mesh, tables, quadrature data, arena)."""
+
+    def __init__(self, dim: int, n, vertices: np.ndarray, order: int, q1: int, gamma: float = 5.0 / 3.0,
+                 cfl: float = 0.5, use_viscosity: bool = True, source: str = "none", precision: str = "fp64",
+                 rho0=None):
+        import torch
+        self.lib = load_library()
+        nx, ny, nz = (n, n, n if dim == 3 else 1) if np.isscalar(n) else (tuple(n) + (1,))[:3]
+        self.dim, self.order, self.q1 = dim, order, q1
+        V = np.ascontiguousarray(vertices, dtype=np.float64)
+        self._verts = V
+        prm = LhParams(dim, nx, ny, nz, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), order, q1,
+                       float(gamma), float(cfl), int(bool(use_viscosity)), SOURCES[source], PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        st = self.lib.lh_setup(ctypes.byref(prm), _ptr(rho0), ctypes.byref(h))
+        if st != LH_OK:
+            raise LhError(st, self.lib.lh_last_error(None).decode())
+        self.h = h
+        s = LhSizes()
+        self._check(self.lib.lh_get_sizes(self.h, ctypes.byref(s)))
+        self.sizes = Sizes(s.ne, s.n_h1, s.nv, s.n_l2, s.nq, s.arena_bytes)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def _check(self, st):
+        if st != LH_OK:
+            raise LhError(st, self.lib.lh_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- buffers -------------------------------------------------------------
+    def h1_vector(self):
+        import torch
+        return torch.zeros((self.dim, self.sizes.n_h1), dtype=torch.float64, device=self.device)
+
+    def l2_vector(self):
+        import torch
+        return torch.zeros((self.sizes.ne, self.sizes.n_l2 // self.sizes.ne), dtype=torch.float64,
+                           device=self.device)
+
+    def new_step_info(self, t: float = 0.0, t_end: float = 0.0):
+        import torch
+        info = LhStepInfo()
+        info.t, info.t_end = t, t_end
+        raw = np.frombuffer(bytes(info), dtype=np.uint8).copy()
+        return torch.from_numpy(raw).to(self.device)
+
+    @staticmethod
+    def read_step_info(buf) -> LhStepInfo:
+        return LhStepInfo.from_buffer_copy(buf.cpu().numpy().tobytes())
+
+    def new_cg_info(self):
+        import torch
+        return torch.zeros(ctypes.sizeof(LhCgInfo), dtype=torch.uint8, device=self.device)
+
+    @staticmethod
+    def read_cg_info(buf) -> LhCgInfo:
+        return LhCgInfo.from_buffer_copy(buf.cpu().numpy().tobytes())
+
+    # --- C ABI calls (same names) --------------------------------------------
+    def init_state(self, problem: str = "taylor_green"):
+        x, v, e = self.h1_vector(), self.h1_vector(), self.l2_vector()
+        self._check(self.lib.lh_init_state(self.h, PROBLEMS[problem], _ptr(x), _ptr(v), _ptr(e), _stream()))
+        return x, v, e
+
+    def update_qdata(self, x, v, e, dt_est=None):
+        self._check(self.lib.lh_update_qdata(self.h, _ptr(x), _ptr(v), _ptr(e), _ptr(dt_est), _stream()))
+
+    def copy_qdata(self, out):
+        self._check(self.lib.lh_copy_qdata(self.h, _ptr(out), _stream()))
+
+    def force_mult(self, u, rhs):
+        self._check(self.lib.lh_force_mult(self.h, _ptr(u), _ptr(rhs), _stream()))
+
+    def force_mult_t(self, v, out):
+        self._check(self.lib.lh_force_mult_t(self.h, _ptr(v), _ptr(out), _stream()))
+
+    def mass_mult(self, x, y):
+        self._check(self.lib.lh_mass_mult(self.h, _ptr(x), _ptr(y), _stream()))
+
+    def mass_cg(self, b, x, rel_tol=1e-12, max_it=1000, info=None):
+        self._check(self.lib.lh_mass_cg(self.h, _ptr(b), _ptr(x), float(rel_tol), int(max_it), _ptr(info),
+                                        _stream()))
+
+    def energy_solve(self, rhs, out):
+        self._check(self.lib.lh_energy_solve(self.h, _ptr(rhs), _ptr(out), _stream()))
+
+    def rk2avg_step(self, x, v, e, dt, info, rel_tol=1e-12, max_it=1000):
+        self._check(self.lib.lh_rk2avg_step(self.h, _ptr(x), _ptr(v), _ptr(e), float(dt), float(rel_tol),
+                                            int(max_it), _ptr(info), _stream()))
+
+    def sync_status(self) -> int:
+        return int(self.lib.lh_sync_status(self.h))
