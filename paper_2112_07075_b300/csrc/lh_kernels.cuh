@@ -65,9 +65,12 @@ __device__ __forceinline__ int axis_owners(int gc, int P, int nel, int (&ee)[2],
   return n;
 }
 
-// Sum over the elements sharing node g of evec[e][c][i] (fixed order).
+// Sum over the elements sharing node g of evec[e][c][i] (fixed order). evec is
+// deliberately not __restrict__: inside the persistent CG kernel other blocks
+// write it between grid barriers, so it must not be read through the
+// non-coherent read-only path.
 template <int DIM, int D>
-__device__ __forceinline__ double gather_node(const MeshDesc &m, const double *__restrict__ evec, int C,
+__device__ __forceinline__ double gather_node(const MeshDesc &m, const double *evec, int C,
                                               int c, int g) {
   constexpr int P = D - 1, ND = ipow<D, DIM>::value;
   int ex[2], ix[2], ey[2], iy[2], ez[2] = {0, 0}, iz[2] = {0, 0};
