@@ -1,0 +1,379 @@
+"""Benchmark of the Lagrange-phase partial-assembly hot path on one B300 per rank.
+
+Workload (default): 3D Taylor-Green vortex on [0,1]^3, 24^3 hexes, H1 Q2 / L2 Q1,
+4^3 Gauss-Legendre points per element, ideal gas gamma = 5/3, FP64, RK2-average
+with CFL 0.5 towards t = 0.1. One benchmark step = one RK2-average step (two
+stages of: quadrature data, F.1, mass CG, F^T v with the energy solve, and the
+state updates), i.e. one pass of the whole hot path.
+
+Metric: MDOF/s = (vector H1 DOFs) x (steps) / (time), 1e6/s, higher is better.
+The L2 cache (126 MB) is flushed before every timed step by writing a 512 MB
+buffer, outside the timed events. Multi-GPU (torchrun): every rank advances its
+own independent replica (the path needs no exchange for independent problems),
+value = all ranks' DOF-steps / max-over-ranks time, scaling "weak".
+
+--impl reference times the FP64 CPU oracle (the method's reference
+implementation, full assembly) on this machine's host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (dim, n, order, q1, jitter, t_end, cfl)
+    "tg3d_24_q2": dict(dim=3, n=24, order=2, q1=4, jitter=0.0, t_end=0.1, cfl=0.5,
+                       desc="3D Taylor-Green, 24^3 hexes, Q2/Q1, 4^3 Gauss points, CFL 0.5 to t=0.1"),
+    "tg2d_8_q2": dict(dim=2, n=8, order=2, q1=4, jitter=0.0, t_end=0.02, cfl=0.5,
+                      desc="2D Taylor-Green, 8^2 quads, Q2/Q1, 4^2 Gauss points"),
+}
+METRIC = "MDOF/s of PA force+mass path (RK2-average step, H1 vector DOFs per second)"
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work model (sum factorization, FP64)
+# ---------------------------------------------------------------------------
+def work_model(dim, p, q1, ne, nh1):
+    D, Q, L = p + 1, q1, p
+    nv = dim * nh1
+    if dim == 3:
+        interp = Q * D ** 3 + Q * Q * D * D + Q ** 3 * D
+        grad = 2 * Q * D ** 3 + 3 * Q * Q * D * D + 3 * Q ** 3 * D
+        l2i = Q * L ** 3 + Q * Q * L * L + Q ** 3 * L
+    else:
+        interp = Q * D * D + Q * Q * D
+        grad = 2 * Q * D * D + 2 * Q * Q * D
+        l2i = Q * L * L + Q * Q * L
+    nq = Q ** dim
+    mass_flops = 2 * ne * (2 * dim * interp) + ne * dim * nq          # FMA = 2 flops, D-scaling 1
+    cg_iter_flops = mass_flops + 10 * nv
+    cg_iter_bytes = 8 * (ne * nq + 2 * nv) + 56 * nv
+    return dict(mass_flops=mass_flops, cg_iter_flops=cg_iter_flops, cg_iter_bytes=cg_iter_bytes,
+                force_flops=2 * ne * dim * grad, force_bytes=8 * (dim * dim * ne * nq + nv),
+                force_t_flops=2 * ne * (dim * grad + l2i) + 2 * ne * dim * dim * nq,
+                force_t_bytes=8 * (dim * dim * ne * nq + nv + ne * L ** dim))
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        smax = max(num(r[2]) or 0 for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+def probe_peaks():
+    path = os.path.join(ROOT, "paper_2112_07075_b300", "probe", "libprobe_alu.so")
+    lib = ctypes.CDLL(path)
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    lib.probe_fma_tflops(ctypes.byref(f64), ctypes.byref(f32))
+    return f64.value, f32.value
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context
+
+    wl = WORKLOADS[args.workload]
+    dim, n, p, q1 = wl["dim"], wl["n"], wl["order"], wl["q1"]
+    V = inputs.box_vertices(dim, n, jitter=wl["jitter"], seed=3 + rank)
+    ctx = Context(dim, n, V, p, q1, cfl=wl["cfl"])
+    sz = ctx.sizes
+    x, v, e = ctx.init_state("taylor_green")
+    info = ctx.new_step_info(0.0, wl["t_end"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    peak64, peak32 = probe_peaks()
+    for _ in range(args.warmup):
+        ctx.rk2avg_step(x, v, e, 0.0, info)
+    torch.cuda.synchronize()
+    if ctx.sync_status() != 0:
+        raise RuntimeError("device status after warm-up: " + ctx.lib.lh_last_error(ctx.h).decode())
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    cg_iters = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(K):
+            flush.fill_(float(k))
+            ev0[k].record(stream)
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_local = sum(step_ms) / 1e3
+    si = ctx.read_step_info(info)
+    status = ctx.sync_status()
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = sz.nv * K * world / t_max / 1e6
+
+    # ---- per-kernel breakdown at the current state (same stream, CUDA events)
+    W = work_model(dim, p, q1, sz.ne, sz.n_h1)
+    reps = 5
+    rhs, acc, out = ctx.h1_vector(), ctx.h1_vector(), ctx.l2_vector()
+    cginfo = ctx.new_cg_info()
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_q = timed(lambda: ctx.update_qdata(x, v, e, None))
+    t_f = timed(lambda: ctx.force_mult(None, rhs))
+    rhs.neg_()
+    iters = []
+
+    def cg():
+        acc.zero_()
+        ctx.mass_cg(rhs, acc, 1e-12, 1000, cginfo)
+    t_cg = timed(cg)
+    cgi = ctx.read_cg_info(cginfo)
+    t_ft = timed(lambda: ctx.force_mult_t(v, out))
+    cg_flops = cgi.iters * W["cg_iter_flops"] + W["mass_flops"]
+    kernels = {
+        "mass_cg": {"ms": t_cg, "iters": cgi.iters, "gflop": cg_flops / 1e9,
+                    "tflops": cg_flops / (t_cg * 1e-3) / 1e12},
+        "qdata": {"ms": t_q},
+        "force_mult": {"ms": t_f, "tflops": W["force_flops"] / (t_f * 1e-3) / 1e12},
+        "force_mult_t": {"ms": t_ft, "tflops": W["force_t_flops"] / (t_ft * 1e-3) / 1e12},
+    }
+    roofline = {"bound": "alu", "kernel": "k_cg (persistent Jacobi-PCG on the PA mass operator)",
+                "achieved": kernels["mass_cg"]["tflops"], "peak": peak64, "unit": "TFLOP/s",
+                "frac": kernels["mass_cg"]["tflops"] / peak64 if peak64 > 0 else None, "traffic": None,
+                "peak_source": "measured FP64 FMA-chain probe (paper_2112_07075_b300/probe/alu_peak.cu), "
+                               "same run; derived 148 SM x 2 DFMA/clk x 2 flop x clock",
+                "flops_per_launch": cg_flops, "fp32_peak_tflops": peak32}
+
+    # ---- end-to-end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty_like(x, device="cpu").pin_memory()
+        vh = torch.empty_like(v, device="cpu").pin_memory()
+        eh = torch.empty_like(e, device="cpu").pin_memory()
+        xh.copy_(x)
+        vh.copy_(v)
+        eh.copy_(e)
+        Ke = max(3, min(K, 10))
+        bytes_io = (xh.numel() + vh.numel() + eh.numel()) * 8
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for k in range(Ke):
+            flush.fill_(2.0)
+            a.record(stream)
+            x.copy_(xh, non_blocking=True)
+            v.copy_(vh, non_blocking=True)
+            e.copy_(eh, non_blocking=True)
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+            xh.copy_(x, non_blocking=True)
+            vh.copy_(v, non_blocking=True)
+            eh.copy_(e, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        e2e = {"value": sz.nv * world / (statistics.mean(ts) * 1e-3) / 1e6, "unit": "MDOF/s",
+               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": Ke}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "dim": dim, "n": n, "order": p, "q1": q1, "cfl": wl["cfl"],
+                       "t_end": wl["t_end"], "nv_per_gpu": sz.nv, "ne": sz.ne, "nq": sz.nq,
+                       "l2_flush": "512 MB buffer written before every timed step",
+                       "parallelism": f"replicas x{world} (independent problems, no exchange)"},
+            "roofline": roofline,
+            "cpu_baseline": None,
+            "e2e": e2e,
+            "gpu_launches": 13 * K,
+            "clocks": clocks,
+            "kernels": kernels,
+            "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
+            "device_status": status, "wall_s_timed": wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, V)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def _cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, V, steps=1):
+    from oracle.hydro import Hydro, Params
+    hy = Hydro(Params(dim=wl["dim"], n=wl["n"], order=wl["order"], q1=wl["q1"], vertices=V, cfl=wl["cfl"]))
+    x, v, e = hy.initial_state("taylor_green")
+    t0 = time.perf_counter()
+    t = 0.0
+    for _ in range(steps):
+        x, v, e, info = hy.rk2avg_step(x, v, e, dt=None, t=t, t_end=wl["t_end"])
+        t += info.dt
+    dt = time.perf_counter() - t0
+    nv = wl["dim"] * hy.mesh.NH1
+    return {"value": nv * steps / dt / 1e6, "unit": "MDOF/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{steps} RK2-average step(s) of the same workload from t=0 (setup excluded), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2112_07075_b300 import inputs
+    from oracle.hydro import Hydro, Params
+    wl = WORKLOADS[args.workload]
+    V = inputs.box_vertices(wl["dim"], wl["n"], jitter=wl["jitter"], seed=3)
+    hy = Hydro(Params(dim=wl["dim"], n=wl["n"], order=wl["order"], q1=wl["q1"], vertices=V, cfl=wl["cfl"]))
+    x, v, e = hy.initial_state("taylor_green")
+    steps = max(1, min(args.steps, 2))
+    t = 0.0
+    x, v, e, info = hy.rk2avg_step(x, v, e, dt=None, t=t, t_end=wl["t_end"])   # warm-up
+    t += info.dt
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, v, e, info = hy.rk2avg_step(x, v, e, dt=None, t=t, t_end=wl["t_end"])
+        t += info.dt
+    el = time.perf_counter() - t0
+    nv = wl["dim"] * hy.mesh.NH1
+    val = nv * steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MDOF/s", "n_gpus": world,
+            "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "dim": wl["dim"], "n": wl["n"], "order": wl["order"],
+                       "q1": wl["q1"]},
+            "cpu_baseline": {"value": val, "unit": "MDOF/s", "cores": _cores(), "kind": "oracle",
+                             "sample": f"{steps} timed RK2-average steps after 1 warm-up step "
+                                       f"(bounded sample of the requested {args.steps})"},
+            "e2e": {"value": val, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tg3d_24_q2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

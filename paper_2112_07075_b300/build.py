@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblh.so")
+PROBE_LIB = os.path.join(HERE, "probe", "libprobe_alu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -33,11 +34,11 @@ def sources():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) \
-        + [os.path.join(HERE, "..", "include", "lh.h")]
+        + [os.path.join(HERE, "..", "include", "lh.h"), os.path.join(HERE, "probe", "alu_peak.cu")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
@@ -65,6 +66,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    probe_src = os.path.join(HERE, "probe", "alu_peak.cu")
+    r = subprocess.run([nvcc, *ARCH, *FLAGS, "-shared", "-o", PROBE_LIB, probe_src], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"probe build failed:\n{r.stdout}\n{r.stderr}")
     return LIB
 
 
