@@ -201,6 +201,39 @@ lh_status lh_energy_solve(lh_ctx *ctx, const double *rhs, double *out, lh_stream
 lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt,
                          double rel_tol, int max_it, lh_step_info *info, lh_stream_t stream);
 
+/* Mass product without any device allocation (the paper has no counterpart; this
+ * is a convenience of this library). Computes the same y = M_v x as lh_mass_mult,
+ * but takes everything from the caller and needs no context, so nothing is
+ * allocated: not by this call and not by an lh_setup before it. It is meant for
+ * callers that may not call cudaMalloc -- for example code that runs inside a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation is not
+ * acceptable, or an embedding application that owns all device memory through its
+ * own pool and forbids other allocations.
+ *
+ * dim, nx, ny, nz (ignored for dim 2), order, q1: as in lh_params (same compiled
+ *   (dim, order, q1) families as lh_setup; LH_ERR_UNSUPPORTED otherwise).
+ * mq: DEVICE [NE][q1^dim], the mass quadrature data omega_q * rho0 * detJ0 at each
+ *   quadrature point (element and point numbering as in the layout notes above).
+ * x, y: DEVICE [dim][N_H1], must not alias; y is overwritten, no boundary
+ *   conditions are applied.
+ * Scratch: the element vector (dim * NE * (order+1)^dim doubles) lives in a
+ *   file-scope static device array of 32 MiB (plus a 4 KiB basis-table array);
+ *   every GPU that loads liblh holds these until the process exits. Larger meshes
+ *   are rejected with LH_ERR_ARG and a message giving the bytes needed, before
+ *   anything is enqueued. The scratch holds the previous call's contents; every
+ *   entry this call reads is written first by this call, so nothing has to start
+ *   at zero.
+ * Set-up: the first call on each device (with that device current) looks up the
+ *   arrays' device addresses with cudaGetSymbolAddress; make that first call
+ *   before any stream capture. The basis table is uploaded on `stream` with a
+ *   cudaMemcpyAsync from host memory at every call.
+ * Concurrency: all calls share the one scratch array per device, so calls whose
+ *   execution overlaps on the GPU (different streams without ordering, or
+ *   several host threads) race and give wrong results; order them on one stream.
+ * Errors: lh_last_error(NULL) describes the last failure of this call. */
+lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int order, int q1, const double *mq,
+                               const double *x, double *y, lh_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -161,6 +161,9 @@ thread_local std::string g_setup_error = "no error";
 
 }  // namespace
 
+// Message returned by lh_last_error(NULL) for calls that have no context.
+void lh::set_global_error(const std::string &msg) { g_setup_error = msg; }
+
 // ---------------------------------------------------------------------------
 // Context
 // ---------------------------------------------------------------------------

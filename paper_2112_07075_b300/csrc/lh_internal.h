@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/lh.h"
 
 namespace lh {
@@ -126,5 +128,8 @@ const Ops *find_ops_3d(int p, int q1);
 void build_tables(int p, int q1, double *tab, int tab_len);
 int table_length(int p, int q1);
 void gll_nodes(int p, double *z);
+
+// Sets the message lh_last_error(NULL) returns (calls without a context).
+void set_global_error(const std::string &msg);
 
 }  // namespace lh

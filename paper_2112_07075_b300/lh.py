@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": 0, "fp32_ir": 1}
 
 EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_status", "lh_init_state",
             "lh_update_qdata", "lh_copy_qdata", "lh_force_mult", "lh_force_mult_t", "lh_mass_mult",
-            "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step"]
+            "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step", "lh_mass_mult_noalloc"]
 
 
 class LhParams(ctypes.Structure):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mass_cg": (I, [P, VP, VP, D, I, VP, VP]),
         "lh_energy_solve": (I, [P, VP, VP, VP]),
         "lh_rk2avg_step": (I, [P, VP, VP, VP, D, D, I, VP, VP]),
+        "lh_mass_mult_noalloc": (I, [I, I, I, I, I, I, VP, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -118,6 +119,18 @@ class Sizes:
     n_l2: int
     nq: int
     arena_bytes: int
+
+
+def mass_mult_noalloc(dim, n, order, q1, mq, x, y):
+    """y = M_v x through lh_mass_mult_noalloc (no context, no device allocation).
+
+    For callers that may not allocate device memory: mq ([NE][q1^dim] quadrature
+    data omega*rho0*detJ0), x and y are caller-owned CUDA tensors."""
+    lib = load_library()
+    nx, ny, nz = (n, n, n if dim == 3 else 1) if np.isscalar(n) else (tuple(n) + (1,))[:3]
+    st = lib.lh_mass_mult_noalloc(dim, nx, ny, nz, order, q1, _ptr(mq), _ptr(x), _ptr(y), _stream())
+    if st != LH_OK:
+        raise LhError(st, lib.lh_last_error(None).decode())
 
 
 class Context:
