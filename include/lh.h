@@ -80,7 +80,11 @@ typedef struct {
   double cfl;               /* CFL number of the time-step estimate (> 0) */
   int use_viscosity;        /* 1: tensor artificial viscosity on, 0: off */
   int source;               /* lh_source */
-  int precision;            /* lh_precision used by lh_rk2avg_step's mass solves */
+  int precision;            /* lh_precision of the velocity mass solves (lh_mass_cg and
+                               lh_rk2avg_step): LH_PRECISION_FP64 = FP64 Jacobi PCG;
+                               LH_PRECISION_FP32_IR = FP32 Jacobi PCG inner solves (FP32
+                               mass data, vectors, contractions) under FP64 iterative
+                               refinement (FP64 residual b - M x, norms, x update) */
 } lh_params;
 
 /* Sizes of a context's spaces. */
@@ -181,8 +185,12 @@ lh_status lh_mass_mult(lh_ctx *ctx, const double *x, double *y, lh_stream_t stre
 /* Velocity mass solve (Eq. 14, "inversion of a global CG mass matrix", Section 6):
  * Jacobi-preconditioned CG for M_v x = b on the free DOFs (v.n = 0 on the box
  * faces; x is set to 0 on constrained DOFs and b is ignored there), stopping when
- * ||r||_2 <= rel_tol ||b||_2 or after max_it iterations. x: in = initial guess,
- * out = solution. b, x: DEVICE [dim][N_H1]. info: DEVICE lh_cg_info or NULL.
+ * the FP64 residual satisfies ||b - M x||_2 <= rel_tol ||b||_2. x: in = initial
+ * guess, out = solution. b, x: DEVICE [dim][N_H1]. info: DEVICE lh_cg_info or NULL.
+ * With the context's precision LH_PRECISION_FP64, max_it bounds the CG iterations;
+ * with LH_PRECISION_FP32_IR each refinement step runs an FP32 PCG to a relative
+ * residual of 1e-5 (at most 200 iterations), at most 40 steps are taken, max_it
+ * bounds the total FP32 iterations, and info->iters reports that total.
  * One persistent cooperative launch; convergence is decided on the device. */
 lh_status lh_mass_cg(lh_ctx *ctx, const double *b, double *x, double rel_tol, int max_it,
                      lh_cg_info *info, lh_stream_t stream);

@@ -143,6 +143,11 @@ __global__ void k_rk_final(size_t nv, double *__restrict__ x, double *__restrict
   }
 }
 
+__global__ void k_to_float(size_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    b[k] = (float)a[k];
+}
+
 __global__ void k_step_finish(lh_step_info *info, const int *status, int has_source) {
   info->t += info->dt;
   info->steps += 1;
@@ -182,6 +187,9 @@ struct lh_ctx {
          *D = nullptr, *me_inv = nullptr, *invdiag = nullptr, *evec = nullptr, *r = nullptr, *pv = nullptr,
          *ap = nullptr, *a_prev = nullptr, *rhs = nullptr, *xh = nullptr, *vh = nullptr, *vb = nullptr,
          *eh = nullptr, *partials = nullptr;
+  float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
+        *evec32 = nullptr;
+  int grid_cg_ir = 0;
   unsigned int *counter = nullptr;
   GridBarrier *bar = nullptr;
   int *dstatus = nullptr;
@@ -258,9 +266,10 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   LH_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
   const Ops &o = *c->ops;
   const size_t smems[] = {o.smem_qdata, o.smem_force, o.smem_force_t, o.smem_mass, o.smem_cg,
-                          o.smem_geom,  o.smem_diag,  o.smem_emass,   o.smem_init_e};
-  void *kerns[] = {o.k_qdata, o.k_force, o.k_force_t, o.k_mass, o.k_cg, o.k_geom, o.k_diag, o.k_emass, o.k_init_e};
-  for (int k = 0; k < 9; ++k)
+                          o.smem_geom,  o.smem_diag,  o.smem_emass,   o.smem_init_e, o.smem_cg_ir};
+  void *kerns[] = {o.k_qdata, o.k_force, o.k_force_t, o.k_mass,   o.k_cg,
+                   o.k_geom,  o.k_diag,  o.k_emass,   o.k_init_e, o.k_cg_ir};
+  for (int k = 0; k < 10; ++k)
     LH_CUDA(c, cudaFuncSetAttribute(kerns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smems[k]));
   c->grid_elem = (m.ne + o.nb - 1) / o.nb;
   int occ = 0;
@@ -269,6 +278,10 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   {
     const int want = std::max(c->grid_elem, grid_for(c->nv, o.threads, 1 << 30));
     c->grid_cg = std::min(occ * c->sms, want);
+    int occ2 = 0;
+    LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, o.k_cg_ir, o.threads, o.smem_cg_ir));
+    if (occ2 < 1) return fail(c, LH_ERR_CUDA, "IR CG kernel cannot be resident");
+    c->grid_cg_ir = std::min(occ2 * c->sms, want);
   }
   c->grid_node = grid_for(c->nv, kNodeThreads, 8 * c->sms * 8);
 
@@ -276,7 +289,9 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   const size_t NE = m.ne, NQ = c->nq, NH1 = m.nh1, NV = c->nv;
   const int tablen = table_length(p, q1);
   const size_t nverts = (size_t)(m.nx + 1) * (m.ny + 1) * (dim == 3 ? m.nz + 1 : 1);
-  const size_t npart = 4 * (size_t)std::max(c->grid_elem, c->grid_cg);
+  const size_t npart = 5 * (size_t)std::max(c->grid_elem, std::max(c->grid_cg, c->grid_cg_ir));
+  const bool ir = prm->precision == LH_PRECISION_FP32_IR;
+  const size_t nf = ir ? 1 : 0;   // FP32 buffers only for the precision form
   struct Item { double **ptr; size_t n; };
   std::vector<Item> items = {
       {&c->tab, (size_t)tablen},       {&c->verts, nverts * dim},   {&c->x0, NV},
@@ -285,7 +300,11 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {&c->evec, NE * dim * c->nd},    {&c->r, NV},                 {&c->pv, NV},
       {&c->ap, NV},                    {&c->a_prev, NV},            {&c->rhs, NV},
       {&c->xh, NV},                    {&c->vh, NV},                {&c->vb, NV},
-      {&c->eh, NE * c->nl},            {&c->partials, npart}};
+      {&c->eh, NE * c->nl},            {&c->partials, npart},
+      {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
+      {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
+      {(double **)&c->ap32, nf * (NV + 1) / 2},       {(double **)&c->d32, nf * (NV + 1) / 2},
+      {(double **)&c->evec32, nf * (NE * dim * c->nd + 1) / 2}};
   size_t bytes = 0;
   for (auto &it : items) bytes += (it.n * sizeof(double) + 255) / 256 * 256;
   const size_t ctl_bytes = 256;
@@ -299,7 +318,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   LH_CUDA(c, cudaMemset(c->arena, 0, bytes));
   size_t off = 0;
   for (auto &it : items) {
-    *it.ptr = (double *)(c->arena + off);
+    *it.ptr = it.n ? (double *)(c->arena + off) : nullptr;
     off += (it.n * sizeof(double) + 255) / 256 * 256;
   }
   char *ctl = c->arena + off;
@@ -348,6 +367,11 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   k_invdiag<<<c->grid_node, kNodeThreads>>>(m, dim, c->r, c->invdiag);
   if (lh_status s = check_launch(c, "invdiag")) return s;
   LH_CUDA(c, cudaMemset(c->r, 0, NV * sizeof(double)));
+  if (ir) {
+    k_to_float<<<grid_for(NE * NQ, kNodeThreads, 65535), kNodeThreads>>>(NE * NQ, c->mq, c->mq32);
+    k_to_float<<<grid_for(NV, kNodeThreads, 65535), kNodeThreads>>>(NV, c->invdiag, c->invdiag32);
+    if (lh_status s = check_launch(c, "fp32 copies")) return s;
+  }
   LH_CUDA(c, cudaDeviceSynchronize());
   return LH_OK;
 }
@@ -487,8 +511,43 @@ lh_status lh_mass_mult(lh_ctx *ctx, const double *x, double *y, lh_stream_t stre
   return check_launch(ctx, "mass gather");
 }
 
+constexpr double kInnerTol = 1e-5;   // FP32 inner solve: relative residual per refinement step
+constexpr int kMaxOuter = 40;
+constexpr int kMaxInner = 200;
+
 static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
                          int *iters_out, double *relres_out, cudaStream_t s) {
+  if (c->prm.precision == LH_PRECISION_FP32_IR) {
+    CgIrArgs a{};
+    a.mesh = c->mesh;
+    a.tab = c->tab;
+    a.mq = c->mq;
+    a.invdiag = c->invdiag;
+    a.b = b;
+    a.mq32 = c->mq32;
+    a.invdiag32 = c->invdiag32;
+    a.x = x;
+    a.evec = c->evec;
+    a.partials = c->partials;
+    a.r32 = c->r32;
+    a.p32 = c->p32;
+    a.ap32 = c->ap32;
+    a.d32 = c->d32;
+    a.evec32 = c->evec32;
+    a.bar = c->bar;
+    a.status = c->dstatus;
+    a.info = info;
+    a.iters_out = iters_out;
+    a.relres_out = relres_out;
+    a.tol = tol;
+    a.inner_tol = kInnerTol;
+    a.max_it = max_it;
+    a.max_outer = kMaxOuter;
+    a.max_inner = kMaxInner;
+    const cudaError_t e = c->ops->cg_ir(a, c->grid_cg_ir, s);
+    if (e != cudaSuccess) return fail(c, LH_ERR_CUDA, std::string("cg_ir launch: ") + cudaGetErrorString(e));
+    return check_launch(c, "cg_ir");
+  }
   CgArgs a{};
   a.mesh = c->mesh;
   a.tab = c->tab;

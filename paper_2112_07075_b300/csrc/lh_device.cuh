@@ -27,18 +27,17 @@ struct ipow<B, 0> { static constexpr int value = 1; };
 // All threads of the block share the work; the caller synchronises.
 // Every output costs K FP64 fused multiply-adds (the first one a multiply).
 // ---------------------------------------------------------------------------
-template <int A, int K, int O, int BS>
-__device__ __forceinline__ void contract(const double *__restrict__ in, double *__restrict__ out,
-                                         const double *__restrict__ M) {
+template <int A, int K, int O, int BS, typename T>
+__device__ __forceinline__ void contract(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ M) {
   constexpr int N = A * O * BS;
   for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
     const int b = idx % BS;
     const int t = idx / BS;
     const int o = t % O;
     const int a = t / O;
-    const double *ip = in + a * K * BS + b;
-    const double *mp = M + o * K;
-    double s = mp[0] * ip[0];
+    const T *ip = in + a * K * BS + b;
+    const T *mp = M + o * K;
+    T s = mp[0] * ip[0];
 #pragma unroll
     for (int k = 1; k < K; ++k) s = fma(mp[k], ip[k * BS], s);
     out[idx] = s;
@@ -87,16 +86,16 @@ __host__ __device__ constexpr int grad_scratch(int C) {
 //   out[c][o_z][o_y][o_x] = sum M[o_x][i_x] M[o_y][i_y] M[o_z][i_z] in[c][i_z][i_y][i_x]
 // for C independent tensors. S: interp_scratch(C) doubles. Ends with a __syncthreads.
 // ---------------------------------------------------------------------------
-template <int DIM, int NI, int NO, int C>
-__device__ __forceinline__ void interp(const double *__restrict__ in, double *__restrict__ out,
-                                       double *__restrict__ S, const double *__restrict__ M) {
+template <int DIM, int NI, int NO, int C, typename T>
+__device__ __forceinline__ void interp(const T *__restrict__ in, T *__restrict__ out, T *__restrict__ S,
+                                       const T *__restrict__ M) {
   if constexpr (DIM == 2) {
     contract<C * NI, NI, NO, 1>(in, S, M);          // x: [C][iy][ox]
     __syncthreads();
     contract<C, NI, NO, NO>(S, out, M);             // y: [C][oy][ox]
     __syncthreads();
   } else {
-    double *t2 = S + C * NI * NI * NO;
+    T *t2 = S + C * NI * NI * NO;
     contract<C * NI * NI, NI, NO, 1>(in, S, M);     // x: [C][iz][iy][ox]
     __syncthreads();
     contract<C * NI, NI, NO, NO>(S, t2, M);         // y: [C][iz][oy][ox]

@@ -77,6 +77,21 @@ struct CgArgs {
   int max_it;
 };
 
+struct CgIrArgs {
+  MeshDesc mesh;
+  const double *tab, *mq, *invdiag, *b;
+  const float *mq32, *invdiag32;
+  double *x, *evec, *partials;
+  float *r32, *p32, *ap32, *d32, *evec32;
+  void *bar;
+  int *status;
+  lh_cg_info *info;
+  int *iters_out;
+  double *relres_out;
+  double tol, inner_tol;
+  int max_it, max_outer, max_inner;
+};
+
 struct GeomArgs {
   MeshDesc mesh;
   const double *tab, *x0, *rho0_in;
@@ -106,13 +121,15 @@ struct InitEArgs {
 // Launchers of one compiled (dim, p, q1) family.
 struct Ops {
   int dim, p, q1, nb, threads;
-  size_t smem_qdata, smem_force, smem_force_t, smem_mass, smem_cg, smem_geom, smem_diag, smem_emass, smem_init_e;
-  void *k_qdata, *k_force, *k_force_t, *k_mass, *k_cg, *k_geom, *k_diag, *k_emass, *k_init_e;
+  size_t smem_qdata, smem_force, smem_force_t, smem_mass, smem_cg, smem_geom, smem_diag, smem_emass, smem_init_e,
+      smem_cg_ir;
+  void *k_qdata, *k_force, *k_force_t, *k_mass, *k_cg, *k_geom, *k_diag, *k_emass, *k_init_e, *k_cg_ir;
   void (*qdata)(const QdataArgs &, int grid, cudaStream_t);
   void (*force)(const ForceArgs &, int grid, cudaStream_t);
   void (*force_t)(const ForceTArgs &, int grid, cudaStream_t);
   void (*mass)(const MassArgs &, int grid, cudaStream_t);
   cudaError_t (*cg)(CgArgs &, int grid, cudaStream_t);
+  cudaError_t (*cg_ir)(CgIrArgs &, int grid, cudaStream_t);
   void (*geom)(const GeomArgs &, int grid, cudaStream_t);
   void (*diag)(const DiagArgs &, int grid, cudaStream_t);
   void (*emass)(const EmassArgs &, int grid, cudaStream_t);

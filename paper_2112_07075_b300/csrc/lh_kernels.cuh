@@ -69,9 +69,8 @@ __device__ __forceinline__ int axis_owners(int gc, int P, int nel, int (&ee)[2],
 // deliberately not __restrict__: inside the persistent CG kernel other blocks
 // write it between grid barriers, so it must not be read through the
 // non-coherent read-only path.
-template <int DIM, int D>
-__device__ __forceinline__ double gather_node(const MeshDesc &m, const double *evec, int C,
-                                              int c, int g) {
+template <int DIM, int D, typename T = double>
+__device__ __forceinline__ T gather_node(const MeshDesc &m, const T *evec, int C, int c, int g) {
   constexpr int P = D - 1, ND = ipow<D, DIM>::value;
   int ex[2], ix[2], ey[2], iy[2], ez[2] = {0, 0}, iz[2] = {0, 0};
   const int gx = g % m.n1x;
@@ -84,7 +83,7 @@ __device__ __forceinline__ double gather_node(const MeshDesc &m, const double *e
     nyo = axis_owners(t % m.n1y, P, m.ny, ey, iy);
     nzo = axis_owners(t / m.n1y, P, m.nz, ez, iz);
   }
-  double s = 0.0;
+  T s = 0;
   for (int a = 0; a < nzo; ++a)
     for (int b = 0; b < nyo; ++b)
       for (int k = 0; k < nxo; ++k) {
@@ -751,6 +750,208 @@ struct Family {
     }
   }
 
+  // ===== precision form: FP32 inner PCG under FP64 iterative refinement ===
+  // Outer (FP64): r = b - M x, ||r|| check, x += d. Inner (FP32): Jacobi PCG on
+  // M d = r from d = 0 to a relative residual inner_tol, FP32 tables, mass data,
+  // vectors and element vectors; dot products summed in FP64.
+  static constexpr int M_S32 = max3(interp_scratch<DIM, D, Q>(CX), interp_scratch<DIM, Q, D>(CX), 0);
+  static constexpr int IR_F = 2 * Q * D + CX * ND + M_S32 + CX * NQ + CX * ND;   // floats
+  static constexpr int IR_D = CX * ND + M_S + CX * NQ + CX * ND;                   // doubles
+  static constexpr int IR_R = (IR_F + 1) / 2 > IR_D ? (IR_F + 1) / 2 : IR_D;
+  static constexpr size_t cg_ir_smem() { return sizeof(double) * (TAB + IR_R + RED); }
+  static __device__ __forceinline__ void body_cg_ir(CgIrArgs a) {
+    extern __shared__ double sm[];
+    double *st = sm, *R = st + TAB, *red = R + IR_R;
+    double *u = R, *S = u + CX * ND, *uq = S + M_S, *y = uq + CX * NQ;                 // FP64 view
+    float *tb = (float *)R, *tbt = tb + Q * D, *uf = tbt + Q * D, *Sf = uf + CX * ND;  // FP32 view
+    float *uqf = Sf + M_S32, *yf = uqf + CX * NQ;
+    __shared__ double s_sc[4];
+    const MeshDesc &m = a.mesh;
+    const int nbatch = (m.ne + NB - 1) / NB;
+    const int G = gridDim.x;
+    const size_t nv = (size_t)DIM * m.nh1;
+    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gstride = (size_t)G * blockDim.x;
+    GridBarrier *bar = (GridBarrier *)a.bar;
+    load_tab(st, a.tab);
+    __syncthreads();
+
+    auto finish = [&](int iters, int status, double rr, double bb) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double bn = sqrt(bb);
+        const double rel = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+        if (a.info) {
+          a.info->iters = iters;
+          a.info->status = status;
+          a.info->rel_res = rel;
+          a.info->b_norm = bn;
+        }
+        if (a.iters_out) *a.iters_out = iters;
+        if (a.relres_out) *a.relres_out = rel;
+        if (status) latch_status(a.status, status);
+      }
+    };
+    auto reduce = [&](int k0, int n) {   // s_sc[k] = sum of partial rows k0..k0+n-1 (fixed order)
+      if (threadIdx.x < 32) {
+        for (int k = 0; k < n; ++k) {
+          const double v = warp_sum_partials(a.partials + (size_t)(k0 + k) * G, G);
+          if (threadIdx.x == 0) s_sc[k0 + k] = v;
+        }
+      }
+      __syncthreads();
+    };
+
+    double bb = 0.0;
+    int inner_total = 0;
+    for (int outer = 0;; ++outer) {
+      // ---- O-A: FP64 E-vector of M x (x masked to the free DOFs)
+      for (int bt = blockIdx.x; bt < nbatch; bt += G) {
+        const int e0 = bt * NB, nb = min(NB, m.ne - e0);
+        for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+          const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+          double val = 0.0;
+          if (b < nb) {
+            const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
+            val = a.invdiag[gi] != 0.0 ? a.x[gi] : 0.0;
+          }
+          u[k] = val;
+        }
+        __syncthreads();
+        mass_elem(st, u, S, uq, y, a.mq, e0, nb);
+        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = y[k];
+        __syncthreads();
+      }
+      if (!grid_sync(bar, a.status)) { finish(inner_total, kStatusTimeout, 0.0, bb); return; }
+      // ---- O-B: FP64 residual, its FP32 copy, inner start d = 0, p = 0
+      {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};  // b.b, r.r (FP64), r32.r32, r32.z32
+        for (size_t k = gtid; k < nv; k += gstride) {
+          const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
+          const double idg = a.invdiag[k];
+          float rf = 0.0f;
+          if (idg != 0.0) {
+            const double bv = a.b[k];
+            const double rv = bv - gather_node<DIM, D>(m, a.evec, DIM, c, gn);
+            acc[0] = fma(bv, bv, acc[0]);
+            acc[1] = fma(rv, rv, acc[1]);
+            rf = (float)rv;
+            const double r2 = (double)rf;
+            acc[2] = fma(r2, r2, acc[2]);
+            acc[3] = fma(r2 * (double)a.invdiag32[k], r2, acc[3]);
+          } else {
+            a.x[k] = 0.0;
+          }
+          a.r32[k] = rf;
+          a.d32[k] = 0.0f;
+          a.p32[k] = 0.0f;
+        }
+        block_sum<4>(acc, red);
+        if (threadIdx.x == 0)
+          for (int q = 0; q < 4; ++q) a.partials[(size_t)q * G + blockIdx.x] = acc[q];
+      }
+      if (!grid_sync(bar, a.status)) { finish(inner_total, kStatusTimeout, 0.0, bb); return; }
+      reduce(0, 4);
+      if (outer == 0) bb = s_sc[0];
+      const double rr64 = s_sc[1];
+      double rr = s_sc[2], rz = s_sc[3], rz_old = rz;
+      if (bb == 0.0) {
+        for (size_t k = gtid; k < nv; k += gstride) a.x[k] = 0.0;
+        finish(0, 0, 0.0, 0.0);
+        return;
+      }
+      if (rr64 <= a.tol * a.tol * bb) { finish(inner_total, 0, rr64, bb); return; }
+      if (outer >= a.max_outer || inner_total >= a.max_it) { finish(inner_total, 5, rr64, bb); return; }
+      // ---- inner FP32 Jacobi PCG on M d = r
+      for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x)
+        tb[k] = (float)(k < Q * D ? st[oB + k] : st[oBt + k - Q * D]);
+      __syncthreads();
+      const double target = a.inner_tol * a.inner_tol * rr;
+      int it = 0;
+      for (;;) {
+        if (rr <= target || it >= a.max_inner) break;
+        const float beta = it == 0 ? 0.0f : (float)(rz / rz_old);
+        rz_old = rz;
+        // I-A: FP32 E-vector of M p_new, p_new = invdiag r + beta p
+        for (int bt = blockIdx.x; bt < nbatch; bt += G) {
+          const int e0 = bt * NB, nb = min(NB, m.ne - e0);
+          for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+            const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+            float val = 0.0f;
+            if (b < nb) {
+              const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
+              val = fmaf(beta, a.p32[gi], a.invdiag32[gi] * a.r32[gi]);
+            }
+            uf[k] = val;
+          }
+          __syncthreads();
+          interp<DIM, D, Q, CX>(uf, uqf, Sf, tb);
+          for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
+            const int q = k % NQ, b = (k / NQ) / DIM;
+            uqf[k] *= b < nb ? a.mq32[(size_t)(e0 + b) * NQ + q] : 0.0f;
+          }
+          __syncthreads();
+          interp<DIM, Q, D, CX>(uqf, yf, Sf, tbt);
+          for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x)
+            a.evec32[(size_t)e0 * DIM * ND + k] = yf[k];
+          __syncthreads();
+        }
+        if (!grid_sync(bar, a.status)) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        // I-B: Ap, p_new, p.Ap
+        {
+          float accf = 0.0f;
+          for (size_t k = gtid; k < nv; k += gstride) {
+            const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
+            const float idg = a.invdiag32[k];
+            float ap = 0.0f, pn = 0.0f;
+            if (idg != 0.0f) {
+              ap = gather_node<DIM, D, float>(m, a.evec32, DIM, c, gn);
+              pn = fmaf(beta, a.p32[k], idg * a.r32[k]);
+              accf = fmaf(pn, ap, accf);
+            }
+            a.ap32[k] = ap;
+            a.p32[k] = pn;
+          }
+          double acc[1] = {(double)accf};
+          block_sum<1>(acc, red);
+          if (threadIdx.x == 0) a.partials[(size_t)4 * G + blockIdx.x] = acc[0];
+        }
+        if (!grid_sync(bar, a.status)) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        reduce(4, 1);
+        const float alpha = (float)(rz / s_sc[4]);
+        // I-C: d += alpha p, r -= alpha Ap, r.r, r.z
+        {
+          float a0 = 0.0f, a1 = 0.0f;
+          for (size_t k = gtid; k < nv; k += gstride) {
+            const float idg = a.invdiag32[k];
+            if (idg != 0.0f) {
+              a.d32[k] = fmaf(alpha, a.p32[k], a.d32[k]);
+              const float rv = fmaf(-alpha, a.ap32[k], a.r32[k]);
+              a.r32[k] = rv;
+              a0 = fmaf(rv, rv, a0);
+              a1 = fmaf(rv * idg, rv, a1);
+            }
+          }
+          double acc[2] = {(double)a0, (double)a1};
+          block_sum<2>(acc, red);
+          if (threadIdx.x == 0) {
+            a.partials[(size_t)2 * G + blockIdx.x] = acc[0];
+            a.partials[(size_t)3 * G + blockIdx.x] = acc[1];
+          }
+        }
+        if (!grid_sync(bar, a.status)) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        reduce(2, 2);
+        rr = s_sc[2];
+        rz = s_sc[3];
+        ++it;
+      }
+      inner_total += it;
+      // ---- x += d (FP64), then every block must see the new x before O-A
+      for (size_t k = gtid; k < nv; k += gstride)
+        if (a.invdiag[k] != 0.0) a.x[k] += (double)a.d32[k];
+      if (!grid_sync(bar, a.status)) { finish(inner_total, kStatusTimeout, rr64, bb); return; }
+    }
+  }
+
   // ===== setup: geometry at qpoints (J0, detJ0, J0^{-1}, mass data) =======
   // smem: tab | u[CX][ND] | S | g[DIM][CX][NQ] | red
   static constexpr int GE_S = grad_scratch<DIM, D, Q>(CX);
@@ -930,6 +1131,8 @@ template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_mass(MassArgs a) { Family<DIM, P, Q>::body_mass(a); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_cg(CgArgs a) { Family<DIM, P, Q>::body_cg(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_cg_ir(CgIrArgs a) { Family<DIM, P, Q>::body_cg_ir(a); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_geom(GeomArgs a) { Family<DIM, P, Q>::body_geom(a); }
 template <int DIM, int P, int Q>

@@ -36,6 +36,11 @@ struct OpsBuilder {
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)k_cg<DIM, P, Q>, dim3(grid), dim3(F::THREADS), args, F::cg_smem(), s);
   }
+  static cudaError_t cg_ir(CgIrArgs &a, int grid, cudaStream_t s) {
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)k_cg_ir<DIM, P, Q>, dim3(grid), dim3(F::THREADS), args,
+                                       F::cg_ir_smem(), s);
+  }
   static void geom(const GeomArgs &a, int grid, cudaStream_t s) {
     k_geom<DIM, P, Q><<<grid, F::THREADS, F::geom_smem(), s>>>(a);
   }
@@ -55,11 +60,12 @@ struct OpsBuilder {
   static const Ops *get() {
     static const Ops ops = {DIM, P, Q, F::NB, F::THREADS,
                             F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
-                            F::geom_smem(), F::diag_smem(), F::emass_smem(), F::init_e_smem(),
+                            F::geom_smem(), F::diag_smem(), F::emass_smem(), F::init_e_smem(), F::cg_ir_smem(),
                             (void *)k_qdata<DIM, P, Q>, (void *)k_force<DIM, P, Q>, (void *)k_force_t<DIM, P, Q>, (void *)k_mass<DIM, P, Q>,
                             (void *)k_cg<DIM, P, Q>, (void *)k_geom<DIM, P, Q>, (void *)k_diag<DIM, P, Q>, (void *)k_emass<DIM, P, Q>,
-                            (void *)k_init_e<DIM, P, Q>,
-                            &qdata, &force, &force_t, &mass, &cg, &geom, &diag, &emass, &init_e, &gather};
+                            (void *)k_init_e<DIM, P, Q>, (void *)k_cg_ir<DIM, P, Q>,
+                            &qdata, &force, &force_t, &mass, &cg, &cg_ir, &geom, &diag, &emass, &init_e,
+                            &gather};
     return &ops;
   }
 };
