@@ -38,6 +38,8 @@ WORKLOADS = {
     # name: (dim, n, order, q1, jitter, t_end, cfl)
     "tg3d_24_q2": dict(dim=3, n=24, order=2, q1=4, jitter=0.0, t_end=0.1, cfl=0.5,
                        desc="3D Taylor-Green, 24^3 hexes, Q2/Q1, 4^3 Gauss points, CFL 0.5 to t=0.1"),
+    "tg3d_32_q4_jit": dict(dim=3, n=32, order=4, q1=6, jitter=0.15, t_end=0.1, cfl=0.5,
+                           desc="3D Taylor-Green, 32^3 hexes jittered +-0.15h (seed 3), Q4/Q3, 6^3 Gauss points"),
     "tg2d_8_q2": dict(dim=2, n=8, order=2, q1=4, jitter=0.0, t_end=0.02, cfl=0.5,
                       desc="2D Taylor-Green, 8^2 quads, Q2/Q1, 4^2 Gauss points"),
 }
@@ -153,7 +155,7 @@ def run_ours(args):
     wl = WORKLOADS[args.workload]
     dim, n, p, q1 = wl["dim"], wl["n"], wl["order"], wl["q1"]
     V = inputs.box_vertices(dim, n, jitter=wl["jitter"], seed=3 + rank)
-    ctx = Context(dim, n, V, p, q1, cfl=wl["cfl"])
+    ctx = Context(dim, n, V, p, q1, cfl=wl["cfl"], precision=args.precision)
     sz = ctx.sizes
     x, v, e = ctx.init_state("taylor_green")
     info = ctx.new_step_info(0.0, wl["t_end"])
@@ -161,6 +163,7 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     peak64, peak32 = probe_peaks()
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         ctx.rk2avg_step(x, v, e, 0.0, info)
     torch.cuda.synchronize()
@@ -174,15 +177,14 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        wall0 = time.perf_counter()
-        for k in range(K):
-            flush.fill_(float(k))
-            ev0[k].record(stream)
-            ctx.rk2avg_step(x, v, e, 0.0, info)
-            ev1[k].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        ctx.rk2avg_step(x, v, e, 0.0, info)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
@@ -233,7 +235,8 @@ def run_ours(args):
         "force_mult": {"ms": t_f, "tflops": W["force_flops"] / (t_f * 1e-3) / 1e12},
         "force_mult_t": {"ms": t_ft, "tflops": W["force_t_flops"] / (t_ft * 1e-3) / 1e12},
     }
-    roofline = {"bound": "alu", "kernel": "k_cg (persistent Jacobi-PCG on the PA mass operator)",
+    roofline = {"bound": "alu", "kernel": "k_cg (persistent Jacobi-PCG on the PA mass operator)"
+                if args.precision == "fp64" else "k_cg_ir (FP32 PCG under FP64 refinement)",
                 "achieved": kernels["mass_cg"]["tflops"], "peak": peak64, "unit": "TFLOP/s",
                 "frac": kernels["mass_cg"]["tflops"] / peak64 if peak64 > 0 else None, "traffic": None,
                 "peak_source": "measured FP64 FMA-chain probe (paper_2112_07075_b300/probe/alu_peak.cu), "
@@ -269,13 +272,19 @@ def run_ours(args):
         e2e = {"value": sz.nv * world / (statistics.mean(ts) * 1e-3) / 1e6, "unit": "MDOF/s",
                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": Ke}
 
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = forms_report(flush)
+    clk.__exit__()
     clocks = clk.summary()
+    clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "dim": dim, "n": n, "order": p, "q1": q1, "cfl": wl["cfl"],
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32(inner CG)",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "precision": args.precision, "dim": dim, "n": n, "order": p, "q1": q1, "cfl": wl["cfl"],
                        "t_end": wl["t_end"], "nv_per_gpu": sz.nv, "ne": sz.ne, "nq": sz.nq,
                        "l2_flush": "512 MB buffer written before every timed step",
                        "parallelism": f"replicas x{world} (independent problems, no exchange)"},
@@ -285,6 +294,7 @@ def run_ours(args):
             "gpu_launches": 13 * K,
             "clocks": clocks,
             "kernels": kernels,
+            "forms": {"precision": forms},
             "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
             "device_status": status, "wall_s_timed": wall,
         }
@@ -294,6 +304,69 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_form(wl_name, precision, steps, warmup, flush, seed=3):
+    """Per-step device time of one form on a workload, and the final state."""
+    import torch
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context
+    wl = WORKLOADS[wl_name]
+    V = inputs.box_vertices(wl["dim"], wl["n"], jitter=wl["jitter"], seed=seed)
+    ctx = Context(wl["dim"], wl["n"], V, wl["order"], wl["q1"], cfl=wl["cfl"], precision=precision)
+    x, v, e = ctx.init_state("taylor_green")
+    info = ctx.new_step_info(0.0, wl["t_end"])
+    stream = torch.cuda.current_stream()
+    ts, iters = [], []
+    for k in range(warmup + steps):
+        flush.fill_(3.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.rk2avg_step(x, v, e, 0.0, info)
+        b.record(stream)
+        b.synchronize()
+        if k >= warmup:
+            ts.append(a.elapsed_time(b))
+            iters.append(list(ctx.read_step_info(info).cg_iters))
+    st = ctx.sync_status()
+    out = dict(ms_per_step=statistics.mean(ts), mdofs=ctx.sizes.nv / (statistics.mean(ts) * 1e-3) / 1e6,
+               cg_iters=iters[-1], status=st, nv=ctx.sizes.nv)
+    # mass-solve cost model at the final state: solves from a zero guess at several tolerances
+    rhs, sol = ctx.h1_vector(), ctx.h1_vector()
+    ctx.force_mult(None, rhs)
+    rhs.neg_()
+    cginfo = ctx.new_cg_info()
+    solves = []
+    for tol in (1e-4, 1e-8, 1e-12):
+        best = None
+        for _ in range(3):
+            sol.zero_()
+            flush.fill_(4.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.mass_cg(rhs, sol, tol, 5000, cginfo)
+            b.record(stream)
+            b.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        ci = ctx.read_cg_info(cginfo)
+        solves.append(dict(tol=tol, ms=best, iters=ci.iters, refinements=ci.refinements, rel_res=ci.rel_res))
+    out["solves_from_zero"] = solves
+    state = tuple(t.cpu().numpy() for t in (x, v, e))
+    ctx.close()
+    return out, state
+
+
+def forms_report(flush, steps=3, warmup=1):
+    rep = {}
+    for wl_name in ("tg3d_24_q2", "tg3d_32_q4_jit"):
+        f64, s64 = measure_form(wl_name, "fp64", steps, warmup, flush)
+        f32, s32 = measure_form(wl_name, "fp32_ir", steps, warmup, flush)
+        err = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(s32, s64))
+        rep[wl_name] = {"fp64": f64, "fp32_ir": f32, "speedup": f64["ms_per_step"] / f32["ms_per_step"],
+                        "max_rel_field_diff_vs_fp64_gpu": err, "steps": warmup + steps,
+                        "note": "same initial state, CFL steps from t=0; per-step CUDA-event time, L2 flushed"}
+    return rep
 
 
 # ---------------------------------------------------------------------------
@@ -366,6 +439,9 @@ def main():
     ap.add_argument("--workload", default="tg3d_24_q2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"],
+                    help="mass-solve precision of the main arm (the headline workload is FP64)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -99,10 +99,12 @@ typedef struct {
 
 /* Result of one mass solve; lives in DEVICE memory. */
 typedef struct {
-  int iters;        /* CG iterations taken */
+  int iters;        /* CG iterations taken (FP32 inner iterations for LH_PRECISION_FP32_IR) */
   int status;       /* LH_OK or LH_ERR_NOT_CONVERGED / LH_ERR_TIMEOUT */
   double rel_res;   /* final ||r||_2 / ||b||_2 (0 when b = 0) */
   double b_norm;    /* ||b||_2 over free DOFs */
+  int refinements;  /* FP64 refinement steps (LH_PRECISION_FP32_IR), 0 otherwise */
+  int reserved;
 } lh_cg_info;
 
 /* Running time-integration record; lives in DEVICE memory. The caller sets t and

@@ -273,15 +273,16 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
     LH_CUDA(c, cudaFuncSetAttribute(kerns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smems[k]));
   c->grid_elem = (m.ne + o.nb - 1) / o.nb;
   int occ = 0;
-  LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, o.k_cg, o.threads, o.smem_cg));
+  LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, o.k_cg, o.threads_cg, o.smem_cg));
   if (occ < 1) return fail(c, LH_ERR_CUDA, "CG kernel cannot be resident");
   {
-    const int want = std::max(c->grid_elem, grid_for(c->nv, o.threads, 1 << 30));
-    c->grid_cg = std::min(occ * c->sms, want);
+    // persistent solvers: at most 2 CTAs per SM (cheaper grid barriers), no more than the work needs
+    const int want = std::max((m.ne + o.nb_cg - 1) / o.nb_cg, grid_for(c->nv / c->dim, o.threads_cg, 1 << 30));
+    c->grid_cg = std::min(std::min(occ, 2) * c->sms, want);
     int occ2 = 0;
-    LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, o.k_cg_ir, o.threads, o.smem_cg_ir));
+    LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, o.k_cg_ir, o.threads_cg, o.smem_cg_ir));
     if (occ2 < 1) return fail(c, LH_ERR_CUDA, "IR CG kernel cannot be resident");
-    c->grid_cg_ir = std::min(occ2 * c->sms, want);
+    c->grid_cg_ir = std::min(std::min(occ2, 2) * c->sms, want);
   }
   c->grid_node = grid_for(c->nv, kNodeThreads, 8 * c->sms * 8);
 
@@ -289,7 +290,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   const size_t NE = m.ne, NQ = c->nq, NH1 = m.nh1, NV = c->nv;
   const int tablen = table_length(p, q1);
   const size_t nverts = (size_t)(m.nx + 1) * (m.ny + 1) * (dim == 3 ? m.nz + 1 : 1);
-  const size_t npart = 5 * (size_t)std::max(c->grid_elem, std::max(c->grid_cg, c->grid_cg_ir));
+  const size_t npart = 8 * (size_t)std::max(c->grid_elem, std::max(c->grid_cg, c->grid_cg_ir));
   const bool ir = prm->precision == LH_PRECISION_FP32_IR;
   const size_t nf = ir ? 1 : 0;   // FP32 buffers only for the precision form
   struct Item { double **ptr; size_t n; };

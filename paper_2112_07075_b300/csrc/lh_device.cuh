@@ -243,43 +243,35 @@ __device__ __forceinline__ void latch_status(int *status, int code) {
 
 // ---------------------------------------------------------------------------
 // Bounded grid barrier for cooperative launches (all blocks co-resident).
-// Counter + generation; the last arriver resets the counter and bumps the
-// generation. Waiters spin with a clock64 limit (about one second) after which
-// they latch LH_ERR_TIMEOUT and report failure; callers then return.
+// A monotonic 64-bit arrival counter, zeroed by the host before each launch:
+// barrier number k (1, 2, ...) of a launch waits until the counter reaches
+// k * gridDim.x. Arrival is a release add (no return value), waiting an acquire
+// load, so the block's writes before the barrier are visible after it. Waiters
+// give up after about one second (clock64), latch LH_ERR_TIMEOUT and report
+// failure; callers then return.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
+  unsigned long long count;
 };
 
 constexpr long long kBarrierSpinCycles = 2000000000LL;  // ~1 s at 2 GHz
 constexpr int kStatusTimeout = 6;                        // LH_ERR_TIMEOUT
 
-__device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *status) {
+__device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned long long target, int *status) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(gb->count);
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(gb->gen);
-    const unsigned int g = gen.load(cuda::memory_order_acquire);
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> cnt(gb->count);
+    cnt.fetch_add(1ull, cuda::memory_order_release);
     int ok = 1;
-    __threadfence();  // make the whole block's writes (ordered by __syncthreads) visible
-    const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-    if (arrived == gridDim.x - 1) {
-      cnt.store(0u, cuda::memory_order_relaxed);
-      gen.store(g + 1u, cuda::memory_order_release);
-    } else {
-      const long long t0 = clock64();
-      while (gen.load(cuda::memory_order_acquire) == g) {
-        if (clock64() - t0 > kBarrierSpinCycles) {
-          ok = 0;
-          latch_status(status, kStatusTimeout);
-          break;
-        }
-        __nanosleep(32);
+    const long long t0 = clock64();
+    while (cnt.load(cuda::memory_order_acquire) < target) {
+      if (clock64() - t0 > kBarrierSpinCycles) {
+        ok = 0;
+        latch_status(status, kStatusTimeout);
+        break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -120,7 +120,7 @@ struct InitEArgs {
 
 // Launchers of one compiled (dim, p, q1) family.
 struct Ops {
-  int dim, p, q1, nb, threads;
+  int dim, p, q1, nb, threads, nb_cg, threads_cg;
   size_t smem_qdata, smem_force, smem_force_t, smem_mass, smem_cg, smem_geom, smem_diag, smem_emass, smem_init_e,
       smem_cg_ir;
   void *k_qdata, *k_force, *k_force_t, *k_mass, *k_cg, *k_geom, *k_diag, *k_emass, *k_init_e, *k_cg_ir;

@@ -33,6 +33,62 @@ __device__ __forceinline__ int h1_node(const MeshDesc &m, int e, int i) {
   }
 }
 
+// Contributions of element-local nodes to H1 node coordinate gc along one axis.
+__device__ __forceinline__ int axis_owners(int gc, int P, int nel, int (&ee)[2], int (&ii)[2]) {
+  const int e = gc / P, i = gc - e * P;
+  if (i != 0) {
+    ee[0] = e;
+    ii[0] = i;
+    return 1;
+  }
+  int n = 0;
+  if (e > 0) { ee[n] = e - 1; ii[n] = P; ++n; }
+  if (e < nel) { ee[n] = e; ii[n] = 0; ++n; }
+  return n;
+}
+
+// Global H1 node of element e's local node (0,0,0): the element's base node.
+template <int DIM, int D>
+__device__ __forceinline__ int h1_base(const MeshDesc &m, int e) {
+  constexpr int P = D - 1;
+  const int ex = e % m.nx, t = e / m.nx;
+  if constexpr (DIM == 2) return ex * P + m.n1x * (t * P);
+  else return ex * P + m.n1x * ((t % m.ny) * P + m.n1y * ((t / m.ny) * P));
+}
+// Offset of local node i from the element's base node (compile-time divisions only).
+template <int DIM, int D>
+__device__ __forceinline__ int h1_local(const MeshDesc &m, int i) {
+  if constexpr (DIM == 2) return i % D + m.n1x * (i / D);
+  else return i % D + m.n1x * ((i / D) % D + m.n1y * (i / (D * D)));
+}
+
+// Offsets e*C*ND + i of every element-local copy of node g in an E-vector with C
+// components (add c*ND for component c), in a fixed order; returns their count.
+template <int DIM, int D>
+__device__ __forceinline__ int node_copies(const MeshDesc &m, int g, int C, int (&off)[1 << DIM]) {
+  constexpr int P = D - 1, ND = ipow<D, DIM>::value;
+  int ex[2], ix[2], ey[2], iy[2], ez[2] = {0, 0}, iz[2] = {0, 0};
+  const int gx = g % m.n1x;
+  const int t = g / m.n1x;
+  const int nxo = axis_owners(gx, P, m.nx, ex, ix);
+  int nyo, nzo = 1;
+  if constexpr (DIM == 2) {
+    nyo = axis_owners(t, P, m.ny, ey, iy);
+  } else {
+    nyo = axis_owners(t % m.n1y, P, m.ny, ey, iy);
+    nzo = axis_owners(t / m.n1y, P, m.nz, ez, iz);
+  }
+  int n = 0;
+  for (int a = 0; a < nzo; ++a)
+    for (int b = 0; b < nyo; ++b)
+      for (int k = 0; k < nxo; ++k) {
+        const int e = ex[k] + m.nx * (ey[b] + m.ny * ez[a]);
+        const int i = ix[k] + D * (iy[b] + D * iz[a]);
+        off[n++] = e * C * ND + i;
+      }
+  return n;
+}
+
 // Is H1 node g constrained for velocity component c (v.n = 0 on the box faces)?
 template <int DIM>
 __device__ __forceinline__ bool h1_constrained(const MeshDesc &m, int g, int c) {
@@ -49,20 +105,6 @@ __device__ __forceinline__ bool h1_constrained(const MeshDesc &m, int g, int c) 
     const int gz = t / m.n1y;
     return gz == 0 || gz == m.n1z - 1;
   }
-}
-
-// Contributions of element-local nodes to H1 node coordinate gc along one axis.
-__device__ __forceinline__ int axis_owners(int gc, int P, int nel, int (&ee)[2], int (&ii)[2]) {
-  const int e = gc / P, i = gc - e * P;
-  if (i != 0) {
-    ee[0] = e;
-    ii[0] = i;
-    return 1;
-  }
-  int n = 0;
-  if (e > 0) { ee[n] = e - 1; ii[n] = P; ++n; }
-  if (e < nel) { ee[n] = e; ii[n] = 0; ++n; }
-  return n;
 }
 
 // Sum over the elements sharing node g of evec[e][c][i] (fixed order). evec is
@@ -331,11 +373,18 @@ struct Family {
                        oBlt = 4 * Q * D + Q * L, oB2t = 4 * Q * D + 2 * Q * L, oW = 5 * Q * D + 2 * Q * L,
                        oIW = oW + Q, oZ = oIW + Q;
   static constexpr int TAB = ((oZ + D) + 1) / 2 * 2;
-  static constexpr int RED = 4 * 32;   // reduction scratch
+  static constexpr int RED_NV = 8;          // block_sum<NV> needs 32*NV doubles: NV <= RED_NV
+  static constexpr int RED = RED_NV * 32;   // reduction scratch (doubles)
 
   static constexpr int CX = NB * DIM;        // one H1 vector field of NB elements
   static constexpr int C2X = NB * 2 * DIM;   // two H1 vector fields
   static constexpr int max3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
+
+  template <int NV>
+  static __device__ __forceinline__ void bsum(double (&v)[NV], double *red) {
+    static_assert(NV <= RED_NV, "reduction scratch too small");
+    block_sum<NV>(v, red);
+  }
 
   static __device__ __forceinline__ void load_tab(double *s, const double *__restrict__ tab) {
     for (int k = threadIdx.x; k < oZ + D; k += blockDim.x) s[k] = tab[k];
@@ -540,7 +589,7 @@ struct Family {
     }
     if (!a.src_sum) return;
     double v1[1] = {src_sum};
-    block_sum<1>(v1, red);
+    bsum<1>(v1, red);
     __shared__ int s_last;
     if (threadIdx.x == 0) {
       a.partials[blockIdx.x] = v1[0];
@@ -590,43 +639,122 @@ struct Family {
   }
 
   // ===== Jacobi-PCG on the PA mass operator (row c2), one persistent launch
-  static constexpr size_t cg_smem() { return mass_smem(); }
+  // CTAs of the persistent solvers are CGM times larger than the element
+  // kernels' (fewer blocks make the grid barriers cheaper).
+  static constexpr int CGM = 2 * THREADS <= 1024 ? 2 : 1;
+  static constexpr int NBC = NB * CGM;          // elements per solver CTA and batch
+  static constexpr int TC = THREADS * CGM;      // threads per solver CTA
+  static constexpr int CXC = NBC * DIM;
+  static constexpr int MC_S = max3(interp_scratch<DIM, D, Q>(CXC), interp_scratch<DIM, Q, D>(CXC), 0);
+
+  // E-vector of M u for one batch: y = B^T diag(mq) B u (CXC tensors), T arithmetic.
+  template <typename T>
+  static __device__ __forceinline__ void batch_matvec(const T *tb, const T *tbt, const T *u, T *S, T *uq, T *y,
+                                                      const T *__restrict__ mq, int e0, int nb) {
+    interp<DIM, D, Q, CXC>(u, uq, S, tb);
+    for (int k = threadIdx.x; k < CXC * NQ; k += blockDim.x) {
+      const int q = k % NQ, b = (k / NQ) / DIM;
+      uq[k] *= b < nb ? mq[(size_t)(e0 + b) * NQ + q] : (T)0;
+    }
+    __syncthreads();
+    interp<DIM, Q, D, CXC>(uq, y, S, tbt);
+  }
+
+  // Search-direction value at a node: p_new = invdiag*(r - alpha q) + beta p (MODE 2),
+  // p0 = invdiag*r (MODE 1), invdiag*r + beta p (MODE 3), or the masked vector x (MODE 0).
+  template <int MODE, typename T>
+  static __device__ __forceinline__ T dir_value(int gi, const T *__restrict__ idv, const T *x, const T *r,
+                                                const T *q, const T *p, T alpha, T beta) {
+    const T idg = idv[gi];
+    if (MODE == 0) return idg != (T)0 ? x[gi] : (T)0;
+    if (MODE == 1) return idg * r[gi];
+    if (MODE == 3) return fma(beta, p[gi], idg * r[gi]);
+    return fma(beta, p[gi], idg * fma(-alpha, q[gi], r[gi]));
+  }
+
+  // One sweep over all element batches: E-vector of M times the MODE vector.
+  template <int MODE, typename T>
+  static __device__ __forceinline__ void sweep_matvec(const MeshDesc &m, int *eb, const T *tb, const T *tbt, T *u,
+                                                      T *S, T *uq, T *y, const T *mq, const T *idv, const T *x,
+                                                      const T *r, const T *q, const T *p, T alpha, T beta,
+                                                      T *evec) {
+    const int nbatch = (m.ne + NBC - 1) / NBC;
+    for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+      const int e0 = bt * NBC, nb = min(NBC, m.ne - e0);
+      if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, e0 + threadIdx.x);
+      __syncthreads();
+      for (int k = threadIdx.x; k < CXC * ND; k += blockDim.x) {
+        const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+        T val = 0;
+        if (b < nb) val = dir_value<MODE, T>(c * m.nh1 + eb[b] + h1_local<DIM, D>(m, i), idv, x, r, q, p, alpha, beta);
+        u[k] = val;
+      }
+      __syncthreads();
+      batch_matvec<T>(tb, tbt, u, S, uq, y, mq, e0, nb);
+      for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) evec[(size_t)e0 * DIM * ND + k] = y[k];
+      __syncthreads();
+    }
+  }
+
+  // Node sweep that closes iteration k and opens k+1 (MODE 2), or starts the
+  // solve (MODE 1: p = invdiag r): r' = r - alpha q, x' = x + alpha p,
+  // p' = invdiag r' + beta p, q' = gathered E-vector; accumulates
+  // (p',q'), (r',z'), (q',z'), (q', invdiag q'), (r',r') into acc[0..4].
+  template <int MODE, typename T>
+  static __device__ __forceinline__ void sweep_nodes(const MeshDesc &m, const T *__restrict__ idv, T *x, T *r, T *q,
+                                                     T *p, const T *evec, T alpha, T beta, T (&acc)[5]) {
+    const int nh1 = m.nh1;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nh1; g += gridDim.x * blockDim.x) {
+      int off[1 << DIM];
+      const int n = node_copies<DIM, D>(m, g, DIM, off);
+      for (int c = 0; c < DIM; ++c) {
+        const int k = c * nh1 + g;
+        const T idg = idv[k];
+        if (idg == (T)0) continue;   // constrained DOF: r, p, q stay 0
+        T rv = r[k], pv = (T)0;
+        if (MODE == 2) {
+          const T pk = p[k];
+          rv = fma(-alpha, q[k], rv);
+          x[k] = fma(alpha, pk, x[k]);
+          pv = fma(beta, pk, idg * rv);
+          r[k] = rv;
+        } else {
+          pv = idg * rv;
+        }
+        T qv = evec[off[0] + c * ND];
+        for (int j = 1; j < n; ++j) qv += evec[off[j] + c * ND];
+        p[k] = pv;
+        q[k] = qv;
+        const T z = idg * rv;
+        acc[0] = fma(pv, qv, acc[0]);
+        acc[1] = fma(rv, z, acc[1]);
+        acc[2] = fma(qv, z, acc[2]);
+        acc[3] = fma(qv * idg, qv, acc[3]);
+        acc[4] = fma(rv, rv, acc[4]);
+      }
+    }
+  }
+
+  static constexpr size_t cg_smem() { return sizeof(double) * (TAB + CXC * ND + MC_S + CXC * NQ + CXC * ND + RED); }
+  // Standard Jacobi PCG, three grid barriers per iteration. (A one-reduction
+  // variant with a scalar recurrence for beta saves a barrier but costs ~5 %
+  // more FP64 operations, which is slower on this FP64-bound kernel.)
   static __device__ __forceinline__ void body_cg(CgArgs a) {
     extern __shared__ double sm[];
-    double *st = sm, *u = st + TAB, *S = u + CX * ND, *uq = S + M_S, *y = uq + CX * NQ, *red = y + CX * ND;
-    __shared__ double s_sc[4];
+    double *st = sm, *u = st + TAB, *S = u + CXC * ND, *uq = S + MC_S, *y = uq + CXC * NQ, *red = y + CXC * ND;
+    __shared__ double s_sc[8];
+    __shared__ int s_eb[NBC];
     const MeshDesc &m = a.mesh;
-    const int nbatch = (m.ne + NB - 1) / NB;
     const int G = gridDim.x;
-    const size_t nv = (size_t)DIM * m.nh1;
-    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t gstride = (size_t)G * blockDim.x;
+    const int nh1 = m.nh1;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gstride = G * blockDim.x;
+    GridBarrier *bar = (GridBarrier *)a.bar;
+    unsigned long long nbar = 0;
+    auto sync = [&]() { ++nbar; return grid_sync(bar, nbar * (unsigned long long)G, a.status); };
     load_tab(st, a.tab);
     __syncthreads();
-
-    // Phase A: E-vector of M applied to (mode 0) the masked initial guess x or
-    // (mode 1) the new search direction p_new = invdiag*r + beta*p_old.
-    auto phase_a = [&](int mode, double beta) {
-      for (int bt = blockIdx.x; bt < nbatch; bt += G) {
-        const int e0 = bt * NB;
-        const int nb = min(NB, m.ne - e0);
-        for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
-          const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
-          double val = 0.0;
-          if (b < nb) {
-            const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
-            const double idg = a.invdiag[gi];
-            if (mode == 0) val = idg != 0.0 ? a.x[gi] : 0.0;
-            else val = fma(beta, a.p[gi], idg * a.r[gi]);
-          }
-          u[k] = val;
-        }
-        __syncthreads();
-        mass_elem(st, u, S, uq, y, a.mq, e0, nb);
-        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = y[k];
-        __syncthreads();
-      }
-    };
+    const double *tb = st + oB, *tbt = st + oBt;
     auto finish = [&](int iters, int status, double rr, double bb) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double bn = sqrt(bb);
@@ -636,54 +764,57 @@ struct Family {
           a.info->status = status;
           a.info->rel_res = rel;
           a.info->b_norm = bn;
+          a.info->refinements = 0;
         }
         if (a.iters_out) *a.iters_out = iters;
         if (a.relres_out) *a.relres_out = rel;
         if (status) latch_status(a.status, status);
       }
     };
-
-    // ---- init: r = b - A x0 on free DOFs, p = z = invdiag r
-    phase_a(0, 0.0);
-    if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(0, kStatusTimeout, 0.0, 0.0); return; }
+    // ---- init: r0 = b - A x0 on free DOFs; x0 = 0 on constrained DOFs
+    sweep_matvec<0, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.x, a.r, a.ap, a.p, 0.0, 0.0, a.evec);
+    if (!sync()) { finish(0, kStatusTimeout, 0.0, 0.0); return; }
     {
-      double acc[3] = {0.0, 0.0, 0.0};  // b.b, r.r, r.z
-      for (size_t k = gtid; k < nv; k += gstride) {
-        const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
-        const double idg = a.invdiag[k];
-        double rv = 0.0;
-        if (idg != 0.0) {
-          const double bv = a.b[k];
-          rv = bv - gather_node<DIM, D>(m, a.evec, DIM, c, gn);
-          acc[0] = fma(bv, bv, acc[0]);
-          acc[1] = fma(rv, rv, acc[1]);
-          acc[2] = fma(rv * idg, rv, acc[2]);
-        } else {
-          a.x[k] = 0.0;
+      double acc[3] = {0.0, 0.0, 0.0};   // b.b, r.r, r.z
+      for (int g = gtid; g < nh1; g += gstride) {
+        int off[1 << DIM];
+        const int n = node_copies<DIM, D>(m, g, DIM, off);
+        for (int c = 0; c < DIM; ++c) {
+          const int k = c * nh1 + g;
+          const double idg = a.invdiag[k];
+          double rv = 0.0;
+          if (idg != 0.0) {
+            double ax = a.evec[off[0] + c * ND];
+            for (int j = 1; j < n; ++j) ax += a.evec[off[j] + c * ND];
+            const double bv = a.b[k];
+            rv = bv - ax;
+            acc[0] = fma(bv, bv, acc[0]);
+            acc[1] = fma(rv, rv, acc[1]);
+            acc[2] = fma(rv * idg, rv, acc[2]);
+          } else {
+            a.x[k] = 0.0;
+          }
+          a.r[k] = rv;
+          a.p[k] = 0.0;
+          a.ap[k] = 0.0;
         }
-        a.r[k] = rv;
-        a.p[k] = idg * rv;
       }
-      block_sum<3>(acc, red);
-      if (threadIdx.x == 0) {
-        a.partials[0 * G + blockIdx.x] = acc[0];
-        a.partials[1 * G + blockIdx.x] = acc[1];
-        a.partials[2 * G + blockIdx.x] = acc[2];
-      }
+      bsum<3>(acc, red);
+      if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) a.partials[(size_t)q * G + blockIdx.x] = acc[q];
     }
-    if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(0, kStatusTimeout, 0.0, 0.0); return; }
+    if (!sync()) { finish(0, kStatusTimeout, 0.0, 0.0); return; }
     if (threadIdx.x < 32) {
-      const double s0 = warp_sum_partials(a.partials, G);
-      const double s1 = warp_sum_partials(a.partials + (size_t)G, G);
-      const double s2 = warp_sum_partials(a.partials + 2 * (size_t)G, G);
-      if (threadIdx.x == 0) { s_sc[0] = s0; s_sc[1] = s1; s_sc[2] = s2; }
+      double v[3];
+      for (int k = 0; k < 3; ++k) v[k] = warp_sum_partials(a.partials + (size_t)k * G, G);
+      if (threadIdx.x == 0) { s_sc[0] = v[0]; s_sc[1] = v[1]; s_sc[2] = v[2]; }
     }
     __syncthreads();
     const double bb = s_sc[0];
-    double rr = s_sc[1], rz = s_sc[2], rz_old = rz;
     const double tol2 = a.tol * a.tol * bb;
+    double rr = s_sc[1], rz = s_sc[2], rz_old = rz;
     if (bb == 0.0) {
-      for (size_t k = gtid; k < nv; k += gstride) a.x[k] = 0.0;
+      for (int k = gtid; k < DIM * nh1; k += gstride) a.x[k] = 0.0;
       finish(0, 0, 0.0, 0.0);
       return;
     }
@@ -691,37 +822,46 @@ struct Family {
     for (;;) {
       if (rr <= tol2) { finish(it, 0, rr, bb); return; }
       if (it >= a.max_it) { finish(it, 5, rr, bb); return; }
-      const double beta = it == 0 ? 0.0 : rz / rz_old;
+      if (threadIdx.x == 0) s_sc[5] = it == 0 ? 0.0 : rz / rz_old;   // beta, once per block
+      __syncthreads();
+      const double beta = s_sc[5];
       rz_old = rz;
-      phase_a(1, beta);
-      if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(it, kStatusTimeout, rr, bb); return; }
-      {  // Phase B: Ap, p_new, p.Ap
+      // E-vector of M p_new, p_new = invdiag r + beta p
+      sweep_matvec<3, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.x, a.r, a.ap, a.p, 0.0, beta,
+                              a.evec);
+      if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
+      {  // q = M p_new, p = p_new, p.q
         double acc[1] = {0.0};
-        for (size_t k = gtid; k < nv; k += gstride) {
-          const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
-          const double idg = a.invdiag[k];
-          double ap = 0.0, pn = 0.0;
-          if (idg != 0.0) {
-            ap = gather_node<DIM, D>(m, a.evec, DIM, c, gn);
-            pn = fma(beta, a.p[k], idg * a.r[k]);
-            acc[0] = fma(pn, ap, acc[0]);
+        for (int g = gtid; g < nh1; g += gstride) {
+          int off[1 << DIM];
+          const int n = node_copies<DIM, D>(m, g, DIM, off);
+          for (int c = 0; c < DIM; ++c) {
+            const int k = c * nh1 + g;
+            const double idg = a.invdiag[k];
+            double qv = 0.0, pn = 0.0;
+            if (idg != 0.0) {
+              qv = a.evec[off[0] + c * ND];
+              for (int j = 1; j < n; ++j) qv += a.evec[off[j] + c * ND];
+              pn = fma(beta, a.p[k], idg * a.r[k]);
+              acc[0] = fma(pn, qv, acc[0]);
+            }
+            a.ap[k] = qv;
+            a.p[k] = pn;
           }
-          a.ap[k] = ap;
-          a.p[k] = pn;
         }
-        block_sum<1>(acc, red);
-        if (threadIdx.x == 0) a.partials[3 * G + blockIdx.x] = acc[0];
+        bsum<1>(acc, red);
+        if (threadIdx.x == 0) a.partials[(size_t)3 * G + blockIdx.x] = acc[0];
       }
-      if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(it, kStatusTimeout, rr, bb); return; }
+      if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
       if (threadIdx.x < 32) {
-        const double s = warp_sum_partials(a.partials + 3 * (size_t)G, G);
-        if (threadIdx.x == 0) s_sc[3] = s;
+        const double v = warp_sum_partials(a.partials + (size_t)3 * G, G);
+        if (threadIdx.x == 0) s_sc[4] = rz / v;   // alpha, once per block
       }
       __syncthreads();
-      const double alpha = rz / s_sc[3];
-      {  // Phase C: x += alpha p, r -= alpha Ap, new r.r and r.z
+      const double alpha = s_sc[4];
+      {  // x += alpha p, r -= alpha q, r.r, r.z
         double acc[2] = {0.0, 0.0};
-        for (size_t k = gtid; k < nv; k += gstride) {
+        for (int k = gtid; k < DIM * nh1; k += gstride) {
           const double idg = a.invdiag[k];
           if (idg != 0.0) {
             a.x[k] = fma(alpha, a.p[k], a.x[k]);
@@ -731,17 +871,17 @@ struct Family {
             acc[1] = fma(rv * idg, rv, acc[1]);
           }
         }
-        block_sum<2>(acc, red);
+        bsum<2>(acc, red);
         if (threadIdx.x == 0) {
-          a.partials[1 * G + blockIdx.x] = acc[0];
-          a.partials[2 * G + blockIdx.x] = acc[1];
+          a.partials[(size_t)1 * G + blockIdx.x] = acc[0];
+          a.partials[(size_t)2 * G + blockIdx.x] = acc[1];
         }
       }
-      if (!grid_sync((GridBarrier *)a.bar, a.status)) { finish(it, kStatusTimeout, rr, bb); return; }
+      if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
       if (threadIdx.x < 32) {
-        const double s1 = warp_sum_partials(a.partials + 1 * (size_t)G, G);
-        const double s2 = warp_sum_partials(a.partials + 2 * (size_t)G, G);
-        if (threadIdx.x == 0) { s_sc[1] = s1; s_sc[2] = s2; }
+        const double v1 = warp_sum_partials(a.partials + (size_t)1 * G, G);
+        const double v2 = warp_sum_partials(a.partials + (size_t)2 * G, G);
+        if (threadIdx.x == 0) { s_sc[1] = v1; s_sc[2] = v2; }
       }
       __syncthreads();
       rr = s_sc[1];
@@ -751,31 +891,36 @@ struct Family {
   }
 
   // ===== precision form: FP32 inner PCG under FP64 iterative refinement ===
-  // Outer (FP64): r = b - M x, ||r|| check, x += d. Inner (FP32): Jacobi PCG on
-  // M d = r from d = 0 to a relative residual inner_tol, FP32 tables, mass data,
-  // vectors and element vectors; dot products summed in FP64.
-  static constexpr int M_S32 = max3(interp_scratch<DIM, D, Q>(CX), interp_scratch<DIM, Q, D>(CX), 0);
-  static constexpr int IR_F = 2 * Q * D + CX * ND + M_S32 + CX * NQ + CX * ND;   // floats
-  static constexpr int IR_D = CX * ND + M_S + CX * NQ + CX * ND;                   // doubles
+  // Outer (FP64): r = b - M x, ||r|| check, x += d. Inner (FP32): the same
+  // two-barrier Jacobi PCG on M d = r from d = 0 to a relative residual
+  // inner_tol, with FP32 tables, mass data, vectors, element vectors, partial
+  // sums and scalars.
+  static constexpr int IR_F = 2 * Q * D + CXC * ND + MC_S + CXC * NQ + CXC * ND;   // floats
+  static constexpr int IR_D = CXC * ND + MC_S + CXC * NQ + CXC * ND;               // doubles
   static constexpr int IR_R = (IR_F + 1) / 2 > IR_D ? (IR_F + 1) / 2 : IR_D;
   static constexpr size_t cg_ir_smem() { return sizeof(double) * (TAB + IR_R + RED); }
   static __device__ __forceinline__ void body_cg_ir(CgIrArgs a) {
     extern __shared__ double sm[];
     double *st = sm, *R = st + TAB, *red = R + IR_R;
-    double *u = R, *S = u + CX * ND, *uq = S + M_S, *y = uq + CX * NQ;                 // FP64 view
-    float *tb = (float *)R, *tbt = tb + Q * D, *uf = tbt + Q * D, *Sf = uf + CX * ND;  // FP32 view
-    float *uqf = Sf + M_S32, *yf = uqf + CX * NQ;
+    double *u = R, *S = u + CXC * ND, *uq = S + MC_S, *y = uq + CXC * NQ;                 // FP64 view
+    float *tb = (float *)R, *tbt = tb + Q * D, *uf = tbt + Q * D, *Sf = uf + CXC * ND;    // FP32 view
+    float *uqf = Sf + MC_S, *yf = uqf + CXC * NQ;
+    float *redf = (float *)red;
     __shared__ double s_sc[4];
+    __shared__ float s_f[4];
+    __shared__ int s_eb[NBC];
     const MeshDesc &m = a.mesh;
-    const int nbatch = (m.ne + NB - 1) / NB;
     const int G = gridDim.x;
-    const size_t nv = (size_t)DIM * m.nh1;
-    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t gstride = (size_t)G * blockDim.x;
+    const int nh1 = m.nh1;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gstride = G * blockDim.x;
+    float *pf = (float *)(a.partials + (size_t)4 * G);   // FP32 partial rows: 5 rows of G floats
     GridBarrier *bar = (GridBarrier *)a.bar;
+    unsigned long long nbar = 0;
+    auto sync = [&]() { ++nbar; return grid_sync(bar, nbar * (unsigned long long)G, a.status); };
     load_tab(st, a.tab);
     __syncthreads();
-
+    int outer = 0;
     auto finish = [&](int iters, int status, double rr, double bb) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double bn = sqrt(bb);
@@ -785,170 +930,187 @@ struct Family {
           a.info->status = status;
           a.info->rel_res = rel;
           a.info->b_norm = bn;
+          a.info->refinements = outer;
         }
         if (a.iters_out) *a.iters_out = iters;
         if (a.relres_out) *a.relres_out = rel;
         if (status) latch_status(a.status, status);
       }
     };
-    auto reduce = [&](int k0, int n) {   // s_sc[k] = sum of partial rows k0..k0+n-1 (fixed order)
-      if (threadIdx.x < 32) {
-        for (int k = 0; k < n; ++k) {
-          const double v = warp_sum_partials(a.partials + (size_t)(k0 + k) * G, G);
-          if (threadIdx.x == 0) s_sc[k0 + k] = v;
-        }
-      }
+    // FP32 block sums of 5 values into thread 0's v (warp shuffles).
+    auto block_sum_f = [&](float (&v)[5]) {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+      for (int k = 0; k < 5; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
       __syncthreads();
+      if (lane == 0)
+        for (int k = 0; k < 5; ++k) redf[k * 32 + warp] = v[k];
+      __syncthreads();
+      if (warp == 0)
+        for (int k = 0; k < 5; ++k) {
+          float t = lane < nw ? redf[k * 32 + lane] : 0.0f;
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          v[k] = t;
+        }
     };
 
-    double bb = 0.0;
+    double bb = -1.0;
     int inner_total = 0;
-    for (int outer = 0;; ++outer) {
+    for (;; ++outer) {
       // ---- O-A: FP64 E-vector of M x (x masked to the free DOFs)
-      for (int bt = blockIdx.x; bt < nbatch; bt += G) {
-        const int e0 = bt * NB, nb = min(NB, m.ne - e0);
-        for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
-          const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
-          double val = 0.0;
-          if (b < nb) {
-            const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
-            val = a.invdiag[gi] != 0.0 ? a.x[gi] : 0.0;
-          }
-          u[k] = val;
-        }
-        __syncthreads();
-        mass_elem(st, u, S, uq, y, a.mq, e0, nb);
-        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = y[k];
-        __syncthreads();
-      }
-      if (!grid_sync(bar, a.status)) { finish(inner_total, kStatusTimeout, 0.0, bb); return; }
-      // ---- O-B: FP64 residual, its FP32 copy, inner start d = 0, p = 0
+      sweep_matvec<0, double>(m, s_eb, st + oB, st + oBt, u, S, uq, y, a.mq, a.invdiag, a.x, a.x, a.x, a.x, 0.0,
+                              0.0, a.evec);
+      if (!sync()) { finish(inner_total, kStatusTimeout, 0.0, 0.0); return; }
+      // ---- O-B: FP64 residual and its FP32 copy; inner start d = 0
       {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};  // b.b, r.r (FP64), r32.r32, r32.z32
-        for (size_t k = gtid; k < nv; k += gstride) {
-          const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
-          const double idg = a.invdiag[k];
-          float rf = 0.0f;
-          if (idg != 0.0) {
-            const double bv = a.b[k];
-            const double rv = bv - gather_node<DIM, D>(m, a.evec, DIM, c, gn);
-            acc[0] = fma(bv, bv, acc[0]);
-            acc[1] = fma(rv, rv, acc[1]);
-            rf = (float)rv;
-            const double r2 = (double)rf;
-            acc[2] = fma(r2, r2, acc[2]);
-            acc[3] = fma(r2 * (double)a.invdiag32[k], r2, acc[3]);
-          } else {
-            a.x[k] = 0.0;
+        double acc[2] = {0.0, 0.0};   // b.b, r.r
+        float accf[5] = {0, 0, 0, 0, 0};   // r32.r32, r32.z32
+        for (int g = gtid; g < nh1; g += gstride) {
+          int off[1 << DIM];
+          const int n = node_copies<DIM, D>(m, g, DIM, off);
+          for (int c = 0; c < DIM; ++c) {
+            const int k = c * nh1 + g;
+            float rf = 0.0f;
+            if (a.invdiag[k] != 0.0) {
+              double ax = a.evec[off[0] + c * ND];
+              for (int j = 1; j < n; ++j) ax += a.evec[off[j] + c * ND];
+              const double bv = a.b[k];
+              const double rv = bv - ax;
+              if (outer == 0) acc[0] = fma(bv, bv, acc[0]);
+              acc[1] = fma(rv, rv, acc[1]);
+              rf = (float)rv;
+              accf[0] = fmaf(rf, rf, accf[0]);
+              accf[1] = fmaf(rf * a.invdiag32[k], rf, accf[1]);
+            } else {
+              a.x[k] = 0.0;
+            }
+            a.r32[k] = rf;
+            a.d32[k] = 0.0f;
+            a.p32[k] = 0.0f;
+            a.ap32[k] = 0.0f;
           }
-          a.r32[k] = rf;
-          a.d32[k] = 0.0f;
-          a.p32[k] = 0.0f;
         }
-        block_sum<4>(acc, red);
-        if (threadIdx.x == 0)
-          for (int q = 0; q < 4; ++q) a.partials[(size_t)q * G + blockIdx.x] = acc[q];
+        bsum<2>(acc, red);
+        if (threadIdx.x == 0) {
+          a.partials[blockIdx.x] = acc[0];
+          a.partials[(size_t)G + blockIdx.x] = acc[1];
+        }
+        block_sum_f(accf);
+        if (threadIdx.x == 0) {
+          pf[blockIdx.x] = accf[0];
+          pf[(size_t)G + blockIdx.x] = accf[1];
+        }
       }
-      if (!grid_sync(bar, a.status)) { finish(inner_total, kStatusTimeout, 0.0, bb); return; }
-      reduce(0, 4);
+      if (!sync()) { finish(inner_total, kStatusTimeout, 0.0, 0.0); return; }
+      if (threadIdx.x < 32) {
+        const double s0 = outer == 0 ? warp_sum_partials(a.partials, G) : 0.0;
+        const double s1 = warp_sum_partials(a.partials + G, G);
+        float f[2];
+        for (int k2 = 0; k2 < 2; ++k2) {
+          float t = 0.0f;
+          for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)k2 * G + i];
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          f[k2] = t;
+        }
+        if (threadIdx.x == 0) { s_sc[0] = s0; s_sc[1] = s1; s_f[0] = f[0]; s_f[1] = f[1]; }
+      }
+      __syncthreads();
       if (outer == 0) bb = s_sc[0];
       const double rr64 = s_sc[1];
-      double rr = s_sc[2], rz = s_sc[3], rz_old = rz;
       if (bb == 0.0) {
-        for (size_t k = gtid; k < nv; k += gstride) a.x[k] = 0.0;
+        for (int k = gtid; k < DIM * nh1; k += gstride) a.x[k] = 0.0;
         finish(0, 0, 0.0, 0.0);
         return;
       }
       if (rr64 <= a.tol * a.tol * bb) { finish(inner_total, 0, rr64, bb); return; }
       if (outer >= a.max_outer || inner_total >= a.max_it) { finish(inner_total, 5, rr64, bb); return; }
-      // ---- inner FP32 Jacobi PCG on M d = r
+      // ---- inner FP32 PCG (standard form, exact dot products, three grid barriers
+      //      per iteration: in FP32 the scalar recurrence of the FP64 solver
+      //      loses too many digits when a step shrinks (r, z) strongly)
       for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x)
         tb[k] = (float)(k < Q * D ? st[oB + k] : st[oBt + k - Q * D]);
       __syncthreads();
-      const double target = a.inner_tol * a.inner_tol * rr;
+      float rr = s_f[0], rz = s_f[1], rz_old = rz;
+      const float target = (float)(a.inner_tol * a.inner_tol) * rr;
       int it = 0;
       for (;;) {
         if (rr <= target || it >= a.max_inner) break;
-        const float beta = it == 0 ? 0.0f : (float)(rz / rz_old);
+        const float beta = it == 0 ? 0.0f : rz / rz_old;
         rz_old = rz;
-        // I-A: FP32 E-vector of M p_new, p_new = invdiag r + beta p
-        for (int bt = blockIdx.x; bt < nbatch; bt += G) {
-          const int e0 = bt * NB, nb = min(NB, m.ne - e0);
-          for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
-            const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
-            float val = 0.0f;
-            if (b < nb) {
-              const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
-              val = fmaf(beta, a.p32[gi], a.invdiag32[gi] * a.r32[gi]);
+        // E: FP32 E-vector of M p_new, p_new = invdiag r + beta p
+        sweep_matvec<3, float>(m, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32, a.p32,
+                               0.0f, beta, a.evec32);
+        if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        {  // q = M p_new gathered, p = p_new, p.q
+          float acc[5] = {0, 0, 0, 0, 0};
+          for (int g = gtid; g < nh1; g += gstride) {
+            int off[1 << DIM];
+            const int n = node_copies<DIM, D>(m, g, DIM, off);
+            for (int c = 0; c < DIM; ++c) {
+              const int k = c * nh1 + g;
+              const float idg = a.invdiag32[k];
+              float qv = 0.0f, pn = 0.0f;
+              if (idg != 0.0f) {
+                qv = a.evec32[off[0] + c * ND];
+                for (int j = 1; j < n; ++j) qv += a.evec32[off[j] + c * ND];
+                pn = fmaf(beta, a.p32[k], idg * a.r32[k]);
+                acc[0] = fmaf(pn, qv, acc[0]);
+              }
+              a.ap32[k] = qv;
+              a.p32[k] = pn;
             }
-            uf[k] = val;
           }
-          __syncthreads();
-          interp<DIM, D, Q, CX>(uf, uqf, Sf, tb);
-          for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
-            const int q = k % NQ, b = (k / NQ) / DIM;
-            uqf[k] *= b < nb ? a.mq32[(size_t)(e0 + b) * NQ + q] : 0.0f;
-          }
-          __syncthreads();
-          interp<DIM, Q, D, CX>(uqf, yf, Sf, tbt);
-          for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x)
-            a.evec32[(size_t)e0 * DIM * ND + k] = yf[k];
-          __syncthreads();
+          block_sum_f(acc);
+          if (threadIdx.x == 0) pf[(size_t)2 * G + blockIdx.x] = acc[0];
         }
-        if (!grid_sync(bar, a.status)) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
-        // I-B: Ap, p_new, p.Ap
-        {
-          float accf = 0.0f;
-          for (size_t k = gtid; k < nv; k += gstride) {
-            const int c = (int)(k / m.nh1), gn = (int)(k % m.nh1);
-            const float idg = a.invdiag32[k];
-            float ap = 0.0f, pn = 0.0f;
-            if (idg != 0.0f) {
-              ap = gather_node<DIM, D, float>(m, a.evec32, DIM, c, gn);
-              pn = fmaf(beta, a.p32[k], idg * a.r32[k]);
-              accf = fmaf(pn, ap, accf);
-            }
-            a.ap32[k] = ap;
-            a.p32[k] = pn;
-          }
-          double acc[1] = {(double)accf};
-          block_sum<1>(acc, red);
-          if (threadIdx.x == 0) a.partials[(size_t)4 * G + blockIdx.x] = acc[0];
+        if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        if (threadIdx.x < 32) {
+          float t = 0.0f;
+          for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)2 * G + i];
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (threadIdx.x == 0) s_f[2] = rz / t;
         }
-        if (!grid_sync(bar, a.status)) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
-        reduce(4, 1);
-        const float alpha = (float)(rz / s_sc[4]);
-        // I-C: d += alpha p, r -= alpha Ap, r.r, r.z
-        {
-          float a0 = 0.0f, a1 = 0.0f;
-          for (size_t k = gtid; k < nv; k += gstride) {
+        __syncthreads();
+        const float alpha = s_f[2];
+        {  // d += alpha p, r -= alpha q, r.r, r.z
+          float acc[5] = {0, 0, 0, 0, 0};
+          for (int k = gtid; k < DIM * nh1; k += gstride) {
             const float idg = a.invdiag32[k];
             if (idg != 0.0f) {
               a.d32[k] = fmaf(alpha, a.p32[k], a.d32[k]);
               const float rv = fmaf(-alpha, a.ap32[k], a.r32[k]);
               a.r32[k] = rv;
-              a0 = fmaf(rv, rv, a0);
-              a1 = fmaf(rv * idg, rv, a1);
+              acc[0] = fmaf(rv, rv, acc[0]);
+              acc[1] = fmaf(rv * idg, rv, acc[1]);
             }
           }
-          double acc[2] = {(double)a0, (double)a1};
-          block_sum<2>(acc, red);
+          block_sum_f(acc);
           if (threadIdx.x == 0) {
-            a.partials[(size_t)2 * G + blockIdx.x] = acc[0];
-            a.partials[(size_t)3 * G + blockIdx.x] = acc[1];
+            pf[(size_t)0 * G + blockIdx.x] = acc[0];
+            pf[(size_t)1 * G + blockIdx.x] = acc[1];
           }
         }
-        if (!grid_sync(bar, a.status)) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
-        reduce(2, 2);
-        rr = s_sc[2];
-        rz = s_sc[3];
+        if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        if (threadIdx.x < 32) {
+          float v[2];
+          for (int k2 = 0; k2 < 2; ++k2) {
+            float t = 0.0f;
+            for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)k2 * G + i];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[k2] = t;
+          }
+          if (threadIdx.x == 0) { s_f[0] = v[0]; s_f[1] = v[1]; }
+        }
+        __syncthreads();
+        rr = s_f[0];
+        rz = s_f[1];
         ++it;
       }
       inner_total += it;
-      // ---- x += d (FP64), then every block must see the new x before O-A
-      for (size_t k = gtid; k < nv; k += gstride)
+      // ---- x += d (FP64); every block must see the new x before O-A
+      for (int k = gtid; k < DIM * nh1; k += gstride)
         if (a.invdiag[k] != 0.0) a.x[k] += (double)a.d32[k];
-      if (!grid_sync(bar, a.status)) { finish(inner_total, kStatusTimeout, rr64, bb); return; }
+      if (!sync()) { finish(inner_total, kStatusTimeout, rr64, bb); return; }
     }
   }
 
@@ -998,7 +1160,7 @@ struct Family {
       vol = fma(w, det, vol);
     }
     double v1[1] = {vol};
-    block_sum<1>(v1, red);
+    bsum<1>(v1, red);
     if (threadIdx.x == 0) a.partials[blockIdx.x] = v1[0];
   }
 
@@ -1130,9 +1292,9 @@ __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force_t(ForceTAr
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_mass(MassArgs a) { Family<DIM, P, Q>::body_mass(a); }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_cg(CgArgs a) { Family<DIM, P, Q>::body_cg(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::TC) k_cg(CgArgs a) { Family<DIM, P, Q>::body_cg(a); }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_cg_ir(CgIrArgs a) { Family<DIM, P, Q>::body_cg_ir(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::TC) k_cg_ir(CgIrArgs a) { Family<DIM, P, Q>::body_cg_ir(a); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_geom(GeomArgs a) { Family<DIM, P, Q>::body_geom(a); }
 template <int DIM, int P, int Q>

@@ -34,11 +34,15 @@ struct OpsBuilder {
   }
   static cudaError_t cg(CgArgs &a, int grid, cudaStream_t s) {
     void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)k_cg<DIM, P, Q>, dim3(grid), dim3(F::THREADS), args, F::cg_smem(), s);
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void *)k_cg<DIM, P, Q>, dim3(grid), dim3(F::TC), args, F::cg_smem(), s);
   }
   static cudaError_t cg_ir(CgIrArgs &a, int grid, cudaStream_t s) {
     void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)k_cg_ir<DIM, P, Q>, dim3(grid), dim3(F::THREADS), args,
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void *)k_cg_ir<DIM, P, Q>, dim3(grid), dim3(F::TC), args,
                                        F::cg_ir_smem(), s);
   }
   static void geom(const GeomArgs &a, int grid, cudaStream_t s) {
@@ -58,7 +62,7 @@ struct OpsBuilder {
     k_gather<DIM, P + 1><<<grid, threads, 0, s>>>(m, evec, C, out, scale, mask);
   }
   static const Ops *get() {
-    static const Ops ops = {DIM, P, Q, F::NB, F::THREADS,
+    static const Ops ops = {DIM, P, Q, F::NB, F::THREADS, F::NBC, F::TC,
                             F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
                             F::geom_smem(), F::diag_smem(), F::emass_smem(), F::init_e_smem(), F::cg_ir_smem(),
                             (void *)k_qdata<DIM, P, Q>, (void *)k_force<DIM, P, Q>, (void *)k_force_t<DIM, P, Q>, (void *)k_mass<DIM, P, Q>,

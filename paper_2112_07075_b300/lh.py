@@ -42,7 +42,7 @@ class LhSizes(ctypes.Structure):
 
 class LhCgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
-                ("b_norm", ctypes.c_double)]
+                ("b_norm", ctypes.c_double), ("refinements", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class LhStepInfo(ctypes.Structure):
