@@ -211,6 +211,47 @@ lh_status lh_energy_solve(lh_ctx *ctx, const double *rhs, double *out, lh_stream
 lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt,
                          double rel_tol, int max_it, lh_step_info *info, lh_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batching form: many independent problems advanced together.
+ *
+ * A batch references existing contexts (2D, q1 = 2*order, LH_PRECISION_FP64;
+ * orders 1..4 may be mixed) and their caller-owned state buffers. Every hot-path
+ * operation of lh_rk2avg_step (quadrature data, F.1, mass CG, F^T v with the
+ * energy solve, state updates) becomes ONE persistent launch over all problems:
+ * element work items are sorted by order and each runs the kernel family of its
+ * order; the mass solves of all problems run in one cooperative launch with
+ * per-problem scalars and convergence (each to rel_tol). The step is captured
+ * into a CUDA graph on first use and replayed. The arithmetic per problem is the
+ * same as lh_rk2avg_step with a fixed dt, except for the summation order of the
+ * CG dot products.
+ * ------------------------------------------------------------------------- */
+typedef struct lh_batch lh_batch;
+
+/* Create a batch of n problems. ctxs[i]: context of problem i; x, v, e: HOST
+ * arrays of n DEVICE pointers to each problem's state (as for lh_rk2avg_step);
+ * dt: HOST array of n fixed step sizes (> 0); infos: DEVICE array of n
+ * lh_step_info records updated by every step (t, dt, steps, cg_iters, cg_rel_res,
+ * status), or NULL. The contexts and buffers must outlive the batch; the batch
+ * owns one small device arena (work lists, argument records, solver scalars). */
+lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *const *v, double *const *e,
+                          const double *dt, lh_step_info *infos, lh_batch **out);
+
+/* Choose, per order, how many element batches one work item holds (1, 2 or 4)
+ * by timing the batched element kernels (which leave the state unchanged).
+ * tiles_out: optional HOST int[4], the chosen tiles for orders 1..4. Synchronous. */
+lh_status lh_batch_autotune(lh_batch *b, int *tiles_out);
+
+/* One RK2-average step of every problem (fixed dt per problem), enqueued on
+ * `stream` as one CUDA graph launch (captured on the first call and whenever
+ * rel_tol or max_it change; rel_tol <= 0: 1e-12, max_it <= 0: 1000). */
+lh_status lh_batch_step(lh_batch *b, double rel_tol, int max_it, lh_stream_t stream);
+
+/* Message of the last error of a batch call. */
+const char *lh_batch_last_error(const lh_batch *b);
+
+/* Release the batch (not its contexts). NULL is accepted. */
+void lh_batch_destroy(lh_batch *b);
+
 /* Mass product without any device allocation (the paper has no counterpart; this
  * is a convenience of this library). Computes the same y = M_v x as lh_mass_mult,
  * but takes everything from the caller and needs no context, so nothing is

@@ -169,33 +169,6 @@ thread_local std::string g_setup_error = "no error";
 // Message returned by lh_last_error(NULL) for calls that have no context.
 void lh::set_global_error(const std::string &msg) { g_setup_error = msg; }
 
-// ---------------------------------------------------------------------------
-// Context
-// ---------------------------------------------------------------------------
-struct lh_ctx {
-  lh_params prm{};
-  MeshDesc mesh{};
-  const Ops *ops = nullptr;
-  int dim = 0, p = 0, q1 = 0, nd = 0, nl = 0, nq = 0;
-  size_t nv = 0;
-  int grid_elem = 0, grid_cg = 0, grid_node = 0, sms = 0;
-  double h0 = 0.0, volume = 0.0;
-  char *arena = nullptr;
-  size_t arena_bytes = 0;
-  // sub-buffers
-  double *tab = nullptr, *verts = nullptr, *x0 = nullptr, *rho0 = nullptr, *mq = nullptr, *jinv0 = nullptr,
-         *D = nullptr, *me_inv = nullptr, *invdiag = nullptr, *evec = nullptr, *r = nullptr, *pv = nullptr,
-         *ap = nullptr, *a_prev = nullptr, *rhs = nullptr, *xh = nullptr, *vh = nullptr, *vb = nullptr,
-         *eh = nullptr, *partials = nullptr;
-  float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
-        *evec32 = nullptr;
-  int grid_cg_ir = 0;
-  unsigned int *counter = nullptr;
-  GridBarrier *bar = nullptr;
-  int *dstatus = nullptr;
-  std::string err = "no error";
-};
-
 static lh_status fail(lh_ctx *c, lh_status s, const std::string &msg) {
   if (c) c->err = msg;
   else g_setup_error = msg;

@@ -1,0 +1,805 @@
+// Batching form: many independent 2D problems of uneven order (p = 1..4,
+// q1 = 2p) and mesh size advanced together. Every hot-path operation of an
+// RK2-average step is ONE persistent launch over all problems: element work
+// items (problem, first element, batch count) sorted by order dispatch to the
+// compiled kernel family of their order; node work items cover node ranges. The
+// mass solves of all problems run in one cooperative launch with per-problem
+// scalars and convergence. The whole step is captured once into a CUDA graph
+// and replayed. Per-order tiles (element batches per work item) are chosen by a
+// timing autotuner. Each problem keeps its own lh_ctx for set-up and buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "lh_kernels.cuh"
+
+namespace lh {
+namespace {
+
+template <int P>
+using F2 = Family<2, P, 2 * P>;
+
+struct ItemE {      // element work item
+  int pid, e0, nbat, order;   // nbat consecutive batches of the family's NB (or NBC) elements
+};
+struct ItemN {      // node work item: scalar H1 nodes [g0, g1) of problem pid
+  int pid, g0, g1, k;   // k = index of this item among the problem's node items
+};
+
+struct BProb {      // per-problem record used by node kernels and the batched solver
+  MeshDesc m;
+  int order, n_nitems, first_nitem, source;
+  const double *tab, *mq, *invdiag, *dt;
+  double *evec, *r, *p, *ap, *a, *rhs;   // a = acceleration (CG solution, warm start)
+  double *x, *v, *e, *xh, *vh, *vb;
+  lh_step_info *info;
+};
+
+struct BScal {      // per-problem CG scalars (device)
+  double bb, rr, rz, rz_old, alpha, beta;
+  int it, active, status, pad;
+  unsigned int cnt, pad2;
+};
+
+constexpr int kThreads = 256;        // element kernels of all 2D families
+constexpr int kThreadsCG = 512;      // batched solver CTAs
+constexpr int kNodeItem = 512;       // nodes per node work item (one per solver thread)
+
+static_assert(F2<1>::THREADS == kThreads && F2<2>::THREADS == kThreads && F2<3>::THREADS == kThreads &&
+                  F2<4>::THREADS == kThreads, "2D families must share the element block size");
+static_assert(F2<1>::TC == kThreadsCG && F2<4>::TC == kThreadsCG, "2D families must share the solver block size");
+
+template <typename F>
+__device__ __forceinline__ void dispatch_order(int order, F &&f) {
+  switch (order) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    default: f(std::integral_constant<int, 4>{}); break;
+  }
+}
+
+// ---- batched element kernels (one launch for all problems) ----------------
+__global__ void __launch_bounds__(kThreads) k_b_qdata(const QdataArgs *args, const ItemE *items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ItemE w = items[it];
+    dispatch_order(w.order, [&](auto P) {
+      using F = F2<decltype(P)::value>;
+      for (int b = 0; b < w.nbat; ++b) {
+        F::body_qdata(args[w.pid], w.e0 + b * F::NB);
+        __syncthreads();
+      }
+    });
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_force(const ForceArgs *args, const ItemE *items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ItemE w = items[it];
+    dispatch_order(w.order, [&](auto P) {
+      using F = F2<decltype(P)::value>;
+      for (int b = 0; b < w.nbat; ++b) {
+        F::body_force(args[w.pid], w.e0 + b * F::NB);
+        __syncthreads();
+      }
+    });
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_b_force_t(const ForceTArgs *args, const ItemE *items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ItemE w = items[it];
+    dispatch_order(w.order, [&](auto P) {
+      using F = F2<decltype(P)::value>;
+      for (int b = 0; b < w.nbat; ++b) {
+        F::body_force_t(args[w.pid], w.e0 + b * F::NB);
+        __syncthreads();
+      }
+    });
+  }
+}
+
+// ---- batched node kernels --------------------------------------------------
+// rhs = -(F.1) gathered from the E-vector, zero on constrained DOFs.
+__global__ void k_b_rhs(const BProb *probs, const ItemN *items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ItemN w = items[it];
+    const BProb &pb = probs[w.pid];
+    const int g = w.g0 + threadIdx.x;
+    if (g < w.g1) {
+      dispatch_order(pb.order, [&](auto P) {
+        constexpr int D = decltype(P)::value + 1, ND = D * D;
+        int off[4];
+        const int n = node_copies<2, D>(pb.m, g, 2, off);
+        for (int c = 0; c < 2; ++c) {
+          const int k = c * pb.m.nh1 + g;
+          double s = pb.evec[off[0] + c * ND];
+          for (int j = 1; j < n; ++j) s += pb.evec[off[j] + c * ND];
+          pb.rhs[k] = pb.invdiag[k] != 0.0 ? -s : 0.0;
+        }
+      });
+    }
+  }
+}
+
+// Stage-1 update: vb0 = v + dt/2 a0, v_h = vb0, x_h = x + dt/2 vb0.
+__global__ void k_b_mid(const BProb *probs, const ItemN *items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ItemN w = items[it];
+    const BProb &pb = probs[w.pid];
+    const int g = w.g0 + threadIdx.x;
+    if (g < w.g1) {
+      const double hdt = 0.5 * *pb.dt;
+      for (int c = 0; c < 2; ++c) {
+        const int k = c * pb.m.nh1 + g;
+        const double vb = fma(hdt, pb.a[k], pb.v[k]);
+        pb.vh[k] = vb;
+        pb.xh[k] = fma(hdt, vb, pb.x[k]);
+      }
+    }
+  }
+}
+
+// Final update: vb = v + dt/2 a, x += dt vb, v += dt a; node item 0 of a problem
+// also advances its step record.
+__global__ void k_b_final(const BProb *probs, const ItemN *items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const ItemN w = items[it];
+    const BProb &pb = probs[w.pid];
+    const int g = w.g0 + threadIdx.x;
+    const double dt = *pb.dt, hdt = 0.5 * dt;
+    if (g < w.g1) {
+      for (int c = 0; c < 2; ++c) {
+        const int k = c * pb.m.nh1 + g;
+        const double ak = pb.a[k], vk = pb.v[k];
+        const double vb = fma(hdt, ak, vk);
+        pb.vb[k] = vb;
+        pb.x[k] = fma(dt, vb, pb.x[k]);
+        pb.v[k] = fma(dt, ak, vk);
+      }
+    }
+    if (w.k == 0 && threadIdx.x == 0 && pb.info) {
+      pb.info->dt = dt;
+      pb.info->t += dt;
+      pb.info->steps += 1;
+    }
+  }
+}
+
+// ---- batched persistent Jacobi PCG -----------------------------------------
+struct BCgArgs {
+  const BProb *probs;
+  BScal *scal;
+  const ItemE *items_e;   // batches of the solver's NBC elements
+  int nitems_e;
+  const ItemN *items_n;
+  int nitems_n, nprob;
+  double *partials;       // [nitems_n][3]
+  int *active;            // number of problems still iterating
+  GridBarrier *bar;
+  int *status;
+  int stage;              // 0 or 1: which cg_iters slot of the step records
+  double tol;
+  int max_it;
+};
+
+template <int P>
+__device__ __forceinline__ void b_cg_matvec(const BProb &pb, int e0, int mode, double beta, double *sm) {
+  using F = F2<P>;
+  constexpr int ND = F::ND, NQ = F::NQ, CXC = F::CXC;
+  double *st = sm, *u = st + F::TAB, *S = u + CXC * ND, *uq = S + F::MC_S, *y = uq + CXC * NQ;
+  __shared__ int s_eb[F2<1>::NBC];
+  const MeshDesc &m = pb.m;
+  const int nb = min(F::NBC, m.ne - e0);
+  for (int k = threadIdx.x; k < F::oZ + F::D; k += blockDim.x) st[k] = pb.tab[k];
+  if (threadIdx.x < nb) s_eb[threadIdx.x] = h1_base<2, F::D>(m, e0 + threadIdx.x);
+  __syncthreads();
+  for (int k = threadIdx.x; k < CXC * ND; k += blockDim.x) {
+    const int i = k % ND, bc = k / ND, c = bc % 2, b = bc / 2;
+    double val = 0.0;
+    if (b < nb) {
+      const int gi = c * m.nh1 + s_eb[b] + h1_local<2, F::D>(m, i);
+      const double idg = pb.invdiag[gi];
+      val = mode == 0 ? (idg != 0.0 ? pb.a[gi] : 0.0) : fma(beta, pb.p[gi], idg * pb.r[gi]);
+    }
+    u[k] = val;
+  }
+  __syncthreads();
+  F::template batch_matvec<double>(st + F::oB, st + F::oBt, u, S, uq, y, pb.mq, e0, nb);
+  for (int k = threadIdx.x; k < nb * 2 * ND; k += blockDim.x) pb.evec[(size_t)e0 * 2 * ND + k] = y[k];
+  __syncthreads();
+}
+
+// Deterministic per-problem reduction of node-item partials: the last item of
+// a problem to finish sums all of them in item order. Returns true in that block.
+__device__ __forceinline__ bool last_item(BScal &sc, int nitems) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&sc.cnt, 1u) == (unsigned)(nitems - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+__device__ __forceinline__ void sum_item_partials(const double *partials, int first, int n, int nv, double *out) {
+  if (threadIdx.x < 32) {
+    __threadfence();
+    for (int q = 0; q < nv; ++q) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < n; i += 32) s += ((volatile const double *)partials)[(size_t)(first + i) * 3 + q];
+      s = warp_sum(s);
+      if (threadIdx.x == 0) out[q] = s;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
+  extern __shared__ double sm[];
+  __shared__ double red[32 * 3];
+  __shared__ double s_v[3];
+  const int G = gridDim.x;
+  unsigned long long nbar = 0;
+  auto sync = [&]() { ++nbar; return grid_sync(A.bar, nbar * (unsigned long long)G, A.status); };
+  const double tol2 = A.tol * A.tol;
+
+  // node phase helper: per node of the item (one thread per scalar node)
+  // ---- init: E-vector of M a (a masked)
+  for (int it = blockIdx.x; it < A.nitems_e; it += G) {
+    const ItemE w = A.items_e[it];
+    const BProb &pb = A.probs[w.pid];
+    dispatch_order(w.order, [&](auto P) {
+      for (int b = 0; b < w.nbat; ++b) b_cg_matvec<decltype(P)::value>(pb, w.e0 + b * F2<decltype(P)::value>::NBC, 0, 0.0, sm);
+    });
+  }
+  if (!sync()) return;
+  // r = b - A a, p = q = 0; partials b.b, r.r, r.z; per-problem reduction
+  for (int it = blockIdx.x; it < A.nitems_n; it += G) {
+    const ItemN w = A.items_n[it];
+    const BProb &pb = A.probs[w.pid];
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int g = w.g0 + threadIdx.x;
+    if (g < w.g1) {
+      dispatch_order(pb.order, [&](auto P) {
+        constexpr int D = decltype(P)::value + 1, ND = D * D;
+        int off[4];
+        const int n = node_copies<2, D>(pb.m, g, 2, off);
+        for (int c = 0; c < 2; ++c) {
+          const int k = c * pb.m.nh1 + g;
+          const double idg = pb.invdiag[k];
+          double rv = 0.0;
+          if (idg != 0.0) {
+            double ax = pb.evec[off[0] + c * ND];
+            for (int j = 1; j < n; ++j) ax += pb.evec[off[j] + c * ND];
+            const double bv = pb.rhs[k];
+            rv = bv - ax;
+            acc[0] = fma(bv, bv, acc[0]);
+            acc[1] = fma(rv, rv, acc[1]);
+            acc[2] = fma(rv * idg, rv, acc[2]);
+          } else {
+            pb.a[k] = 0.0;
+          }
+          pb.r[k] = rv;
+          pb.p[k] = 0.0;
+          pb.ap[k] = 0.0;
+        }
+      });
+    }
+    block_sum<3>(acc, red);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 3; ++q) A.partials[(size_t)it * 3 + q] = acc[q];
+    BScal &sc = A.scal[w.pid];
+    if (last_item(sc, pb.n_nitems)) {
+      sum_item_partials(A.partials, pb.first_nitem, pb.n_nitems, 3, s_v);
+      if (threadIdx.x == 0) {
+        sc.cnt = 0;
+        sc.bb = s_v[0];
+        sc.rr = s_v[1];
+        sc.rz = s_v[2];
+        sc.rz_old = s_v[2];
+        sc.beta = 0.0;
+        sc.it = 0;
+        sc.status = 0;
+        sc.active = (s_v[0] > 0.0 && s_v[1] > tol2 * s_v[0]) ? 1 : 0;
+        if (sc.active) atomicAdd(A.active, 1);
+      }
+    }
+  }
+  if (!sync()) return;
+
+  for (int iter = 0;; ++iter) {
+    const int nact = *(volatile int *)A.active;
+    if (nact == 0 || iter >= A.max_it) break;
+    // E: element matvec of p_new = invdiag r + beta p for active problems
+    for (int it = blockIdx.x; it < A.nitems_e; it += G) {
+      const ItemE w = A.items_e[it];
+      const BScal &sc = A.scal[w.pid];
+      if (!sc.active) continue;
+      const BProb &pb = A.probs[w.pid];
+      const double beta = sc.beta;
+      dispatch_order(w.order, [&](auto P) {
+        for (int b = 0; b < w.nbat; ++b)
+          b_cg_matvec<decltype(P)::value>(pb, w.e0 + b * F2<decltype(P)::value>::NBC, 1, beta, sm);
+      });
+    }
+    if (!sync()) return;
+    // B: q = M p_new, p = p_new, p.q; alpha per problem
+    for (int it = blockIdx.x; it < A.nitems_n; it += G) {
+      const ItemN w = A.items_n[it];
+      BScal &sc = A.scal[w.pid];
+      if (!sc.active) continue;
+      const BProb &pb = A.probs[w.pid];
+      const double beta = sc.beta;
+      double acc[3] = {0.0, 0.0, 0.0};
+      const int g = w.g0 + threadIdx.x;
+      if (g < w.g1) {
+        dispatch_order(pb.order, [&](auto P) {
+          constexpr int D = decltype(P)::value + 1, ND = D * D;
+          int off[4];
+          const int n = node_copies<2, D>(pb.m, g, 2, off);
+          for (int c = 0; c < 2; ++c) {
+            const int k = c * pb.m.nh1 + g;
+            const double idg = pb.invdiag[k];
+            double qv = 0.0, pn = 0.0;
+            if (idg != 0.0) {
+              qv = pb.evec[off[0] + c * ND];
+              for (int j = 1; j < n; ++j) qv += pb.evec[off[j] + c * ND];
+              pn = fma(beta, pb.p[k], idg * pb.r[k]);
+              acc[0] = fma(pn, qv, acc[0]);
+            }
+            pb.ap[k] = qv;
+            pb.p[k] = pn;
+          }
+        });
+      }
+      block_sum<3>(acc, red);
+      if (threadIdx.x == 0) A.partials[(size_t)it * 3] = acc[0];
+      if (last_item(sc, pb.n_nitems)) {
+        sum_item_partials(A.partials, pb.first_nitem, pb.n_nitems, 1, s_v);
+        if (threadIdx.x == 0) {
+          sc.cnt = 0;
+          sc.alpha = sc.rz / s_v[0];
+        }
+      }
+    }
+    if (!sync()) return;
+    // C: a += alpha p, r -= alpha q, r.r, r.z; convergence and beta per problem
+    for (int it = blockIdx.x; it < A.nitems_n; it += G) {
+      const ItemN w = A.items_n[it];
+      BScal &sc = A.scal[w.pid];
+      if (!sc.active) continue;
+      const BProb &pb = A.probs[w.pid];
+      const double alpha = sc.alpha;
+      double acc[3] = {0.0, 0.0, 0.0};
+      const int g = w.g0 + threadIdx.x;
+      if (g < w.g1) {
+        for (int c = 0; c < 2; ++c) {
+          const int k = c * pb.m.nh1 + g;
+          const double idg = pb.invdiag[k];
+          if (idg != 0.0) {
+            pb.a[k] = fma(alpha, pb.p[k], pb.a[k]);
+            const double rv = fma(-alpha, pb.ap[k], pb.r[k]);
+            pb.r[k] = rv;
+            acc[0] = fma(rv, rv, acc[0]);
+            acc[1] = fma(rv * idg, rv, acc[1]);
+          }
+        }
+      }
+      block_sum<3>(acc, red);
+      if (threadIdx.x == 0) {
+        A.partials[(size_t)it * 3] = acc[0];
+        A.partials[(size_t)it * 3 + 1] = acc[1];
+      }
+      if (last_item(sc, pb.n_nitems)) {
+        sum_item_partials(A.partials, pb.first_nitem, pb.n_nitems, 2, s_v);
+        if (threadIdx.x == 0) {
+          sc.cnt = 0;
+          sc.it += 1;
+          sc.rr = s_v[0];
+          sc.rz_old = sc.rz;
+          sc.rz = s_v[1];
+          sc.beta = sc.rz / sc.rz_old;
+          if (sc.rr <= tol2 * sc.bb) {
+            sc.active = 0;
+            atomicSub(A.active, 1);
+          } else if (sc.it >= A.max_it) {
+            sc.active = 0;
+            sc.status = 5;
+            atomicSub(A.active, 1);
+            latch_status(A.status, 5);
+          }
+        }
+      }
+    }
+    if (!sync()) return;
+  }
+  // report per problem; problems with b = 0 get a = 0
+  for (int pid = blockIdx.x; pid < A.nprob; pid += G) {
+    const BProb &pb = A.probs[pid];
+    const BScal &sc = A.scal[pid];
+    if (sc.bb == 0.0)
+      for (int k = threadIdx.x; k < 2 * pb.m.nh1; k += blockDim.x) pb.a[k] = 0.0;
+    if (threadIdx.x == 0 && pb.info) {
+      pb.info->cg_iters[A.stage] = sc.it;
+      pb.info->cg_rel_res[A.stage] = sc.bb > 0.0 ? sqrt(sc.rr / sc.bb) : 0.0;
+      if (sc.status) pb.info->status = sc.status;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace lh
+
+using namespace lh;
+
+struct lh_batch {
+  int n = 0;
+  std::vector<lh_ctx *> ctx;
+  std::vector<int> order;
+  int tiles[5] = {0, 1, 1, 1, 1};   // element batches per work item, per order (autotuned)
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  // device arrays
+  QdataArgs *q1 = nullptr, *q2 = nullptr;
+  ForceArgs *fa = nullptr;
+  ForceTArgs *t1 = nullptr, *t2 = nullptr;
+  BProb *probs = nullptr;
+  BScal *scal = nullptr;
+  ItemE *items_e = nullptr, *items_cg = nullptr;
+  ItemN *items_n = nullptr;
+  int n_items_e = 0, n_items_cg = 0, n_items_n = 0, cap_items_e = 0;
+  double *partials = nullptr, *dts = nullptr;
+  int *active = nullptr, *status = nullptr;
+  GridBarrier *bar = nullptr;
+  int grid_e = 0, grid_n = 0, grid_cg = 0;
+  size_t smem_e = 0, smem_cg = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double graph_tol = -1.0;
+  int graph_max_it = -1;
+  lh_step_info *graph_info = nullptr;
+  std::string err;
+};
+
+static lh_status bfail(lh_batch *b, lh_status s, const std::string &msg) {
+  if (b) b->err = msg;
+  lh::set_global_error(msg);
+  return s;
+}
+
+#define BCUDA(b, call)                                                                          \
+  do {                                                                                          \
+    cudaError_t _e = (call);                                                                    \
+    if (_e != cudaSuccess) return bfail((b), LH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+static int nb_of(int order) {
+  switch (order) {
+    case 1: return F2<1>::NB;
+    case 2: return F2<2>::NB;
+    case 3: return F2<3>::NB;
+    default: return F2<4>::NB;
+  }
+}
+static int nbc_of(int order) {
+  switch (order) {
+    case 1: return F2<1>::NBC;
+    case 2: return F2<2>::NBC;
+    case 3: return F2<3>::NBC;
+    default: return F2<4>::NBC;
+  }
+}
+
+// Element work items of all problems, sorted by order, `tiles[p]` batches of `nbf(p)` elements each.
+template <typename NBF>
+static std::vector<ItemE> make_items(const lh_batch *b, const int *tiles, NBF nbf) {
+  std::vector<ItemE> items;
+  for (int p = 1; p <= 4; ++p)
+    for (int i = 0; i < b->n; ++i) {
+      if (b->order[i] != p) continue;
+      const int ne = b->ctx[i]->mesh.ne, nb = nbf(p), tile = std::max(1, tiles[p]);
+      const int nbat = (ne + nb - 1) / nb;
+      for (int bt = 0; bt < nbat; bt += tile) items.push_back({i, bt * nb, std::min(tile, nbat - bt), p});
+    }
+  return items;
+}
+
+static lh_status upload_items(lh_batch *b) {
+  std::vector<ItemE> ie = make_items(b, b->tiles, nb_of);
+  if ((int)ie.size() > b->cap_items_e) return bfail(b, LH_ERR_ARG, "work list larger than at creation");
+  BCUDA(b, cudaMemcpy(b->items_e, ie.data(), ie.size() * sizeof(ItemE), cudaMemcpyHostToDevice));
+  b->n_items_e = (int)ie.size();
+  return LH_OK;
+}
+
+extern "C" {
+
+void lh_batch_destroy(lh_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->arena) cudaFree(b->arena);
+  delete b;
+}
+
+const char *lh_batch_last_error(const lh_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *const *v, double *const *e,
+                          const double *dt, lh_step_info *infos, lh_batch **out) {
+  if (!out) return bfail(nullptr, LH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !ctxs || !x || !v || !e || !dt) return bfail(nullptr, LH_ERR_ARG, "bad batch arguments");
+  lh_batch *b = new lh_batch();
+  b->n = n;
+  for (int i = 0; i < n; ++i) {
+    lh_ctx *c = ctxs[i];
+    if (!c || !x[i] || !v[i] || !e[i]) { lh_batch_destroy(b); return bfail(nullptr, LH_ERR_ARG, "null problem"); }
+    if (c->dim != 2 || c->q1 != 2 * c->p || c->prm.precision != LH_PRECISION_FP64) {
+      lh_batch_destroy(b);
+      return bfail(nullptr, LH_ERR_UNSUPPORTED, "batched problems must be 2D, q1 = 2p, FP64");
+    }
+    if (!(dt[i] > 0.0)) { lh_batch_destroy(b); return bfail(nullptr, LH_ERR_ARG, "dt must be > 0"); }
+    b->ctx.push_back(c);
+    b->order.push_back(c->p);
+  }
+  // work lists (element items with the largest tile count used later must fit: size with tile 1)
+  const int tiles1[5] = {0, 1, 1, 1, 1};
+  std::vector<ItemE> ie = make_items(b, tiles1, nb_of);
+  std::vector<ItemE> ic = make_items(b, tiles1, nbc_of);
+  std::vector<ItemN> in;
+  std::vector<BProb> pr(n);
+  for (int i = 0; i < n; ++i) {
+    lh_ctx *c = b->ctx[i];
+    const int first = (int)in.size(), nh1 = c->mesh.nh1;
+    int k = 0;
+    for (int g0 = 0; g0 < nh1; g0 += kNodeItem, ++k) in.push_back({i, g0, std::min(nh1, g0 + kNodeItem), k});
+    BProb &p = pr[i];
+    p.m = c->mesh;
+    p.order = c->p;
+    p.n_nitems = (int)in.size() - first;
+    p.first_nitem = first;
+    p.source = c->prm.source;
+    p.tab = c->tab;
+    p.mq = c->mq;
+    p.invdiag = c->invdiag;
+    p.evec = c->evec;
+    p.r = c->r;
+    p.p = c->pv;
+    p.ap = c->ap;
+    p.a = c->a_prev;
+    p.rhs = c->rhs;
+    p.x = x[i];
+    p.v = v[i];
+    p.e = e[i];
+    p.xh = c->xh;
+    p.vh = c->vh;
+    p.vb = c->vb;
+    p.info = infos ? infos + i : nullptr;
+  }
+  // arena
+  struct Item { void **ptr; size_t bytes; };
+  const size_t nie = ie.size(), nic = ic.size(), nin = in.size();
+  std::vector<Item> items = {
+      {(void **)&b->q1, n * sizeof(QdataArgs)},   {(void **)&b->q2, n * sizeof(QdataArgs)},
+      {(void **)&b->fa, n * sizeof(ForceArgs)},   {(void **)&b->t1, n * sizeof(ForceTArgs)},
+      {(void **)&b->t2, n * sizeof(ForceTArgs)},  {(void **)&b->probs, n * sizeof(BProb)},
+      {(void **)&b->scal, n * sizeof(BScal)},     {(void **)&b->items_e, nie * sizeof(ItemE)},
+      {(void **)&b->items_cg, nic * sizeof(ItemE)}, {(void **)&b->items_n, nin * sizeof(ItemN)},
+      {(void **)&b->partials, nin * 3 * sizeof(double)}, {(void **)&b->dts, n * sizeof(double)},
+      {(void **)&b->active, 64}, {(void **)&b->status, 64}, {(void **)&b->bar, 64}};
+  size_t bytes = 0;
+  for (auto &it : items) bytes += (it.bytes + 255) / 256 * 256;
+  if (cudaMalloc(&b->arena, bytes) != cudaSuccess) {
+    b->arena = nullptr;
+    lh_batch_destroy(b);
+    return bfail(nullptr, LH_ERR_OOM, "batch arena allocation failed");
+  }
+  b->arena_bytes = bytes;
+  size_t off = 0;
+  for (auto &it : items) {
+    *it.ptr = b->arena + off;
+    off += (it.bytes + 255) / 256 * 256;
+  }
+  cudaMemset(b->arena, 0, bytes);
+  for (int i = 0; i < n; ++i) pr[i].dt = b->dts + i;
+  // per-problem argument structs
+  std::vector<QdataArgs> q1(n), q2(n);
+  std::vector<ForceArgs> fa(n);
+  std::vector<ForceTArgs> t1(n), t2(n);
+  for (int i = 0; i < n; ++i) {
+    lh_ctx *c = b->ctx[i];
+    QdataArgs q{};
+    q.mesh = c->mesh;
+    q.tab = c->tab;
+    q.mq = c->mq;
+    q.jinv0 = c->jinv0;
+    q.D = c->D;
+    q.phys.gamma = c->prm.gamma;
+    q.phys.h0 = c->h0;
+    q.phys.order = (double)c->p;
+    q.phys.use_viscosity = c->prm.use_viscosity;
+    q.want_dt = 0;
+    q.cfl = c->prm.cfl;
+    q.status = c->dstatus;
+    q.x = x[i];
+    q.v = v[i];
+    q.e = e[i];
+    q1[i] = q;
+    q.x = c->xh;
+    q.v = c->vh;
+    q.e = c->eh;
+    q2[i] = q;
+    fa[i] = ForceArgs{c->mesh, c->tab, c->D, nullptr, c->evec};
+    const bool src = c->prm.source == LH_SOURCE_TAYLOR_GREEN_2D;
+    ForceTArgs t{};
+    t.mesh = c->mesh;
+    t.tab = c->tab;
+    t.D = c->D;
+    t.mq = c->mq;
+    t.me_inv = c->me_inv;
+    t.dt = b->dts + i;
+    t.v = c->vh;
+    t.src_x = src ? x[i] : nullptr;
+    t.e_base = e[i];
+    t.coef = 0.5;
+    t.out = c->eh;
+    t1[i] = t;
+    t.v = c->vb;
+    t.src_x = src ? c->xh : nullptr;
+    t.coef = 1.0;
+    t.out = e[i];
+    t2[i] = t;
+  }
+  BCUDA(b, cudaMemcpy(b->q1, q1.data(), n * sizeof(QdataArgs), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->q2, q2.data(), n * sizeof(QdataArgs), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->fa, fa.data(), n * sizeof(ForceArgs), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->t1, t1.data(), n * sizeof(ForceTArgs), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->t2, t2.data(), n * sizeof(ForceTArgs), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->probs, pr.data(), n * sizeof(BProb), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->dts, dt, n * sizeof(double), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->items_e, ie.data(), nie * sizeof(ItemE), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->items_cg, ic.data(), nic * sizeof(ItemE), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->items_n, in.data(), nin * sizeof(ItemN), cudaMemcpyHostToDevice));
+  b->n_items_e = (int)nie;
+  b->cap_items_e = (int)nie;
+  b->n_items_cg = (int)nic;
+  b->n_items_n = (int)nin;
+  // launch shapes: shared memory = largest family's need
+  b->smem_e = std::max({F2<1>::qdata_smem(), F2<2>::qdata_smem(), F2<3>::qdata_smem(), F2<4>::qdata_smem(),
+                        F2<1>::force_smem(), F2<2>::force_smem(), F2<3>::force_smem(), F2<4>::force_smem(),
+                        F2<1>::force_t_smem(), F2<2>::force_t_smem(), F2<3>::force_t_smem(),
+                        F2<4>::force_t_smem()});
+  b->smem_cg = std::max({F2<1>::cg_smem(), F2<2>::cg_smem(), F2<3>::cg_smem(), F2<4>::cg_smem()});
+  const void *ke[] = {(const void *)k_b_qdata, (const void *)k_b_force, (const void *)k_b_force_t};
+  int sms = 0, dev = 0, occ = 0;
+  BCUDA(b, cudaGetDevice(&dev));
+  BCUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int occ_e = 1 << 30;
+  for (const void *k : ke) {
+    BCUDA(b, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_e));
+    BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, b->smem_e));
+    occ_e = std::min(occ_e, occ);
+  }
+  b->grid_e = std::max(1, occ_e) * sms;
+  BCUDA(b, cudaFuncSetAttribute((const void *)k_b_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_cg));
+  BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_b_cg, kThreadsCG, b->smem_cg));
+  if (occ < 1) { lh_batch_destroy(b); return bfail(nullptr, LH_ERR_CUDA, "batched solver cannot be resident"); }
+  b->grid_cg = std::min(occ, 2) * sms;
+  b->grid_n = 4 * sms;
+  BCUDA(b, cudaDeviceSynchronize());
+  *out = b;
+  return LH_OK;
+}
+
+static lh_status enqueue_step(lh_batch *b, double tol, int max_it, cudaStream_t s) {
+  const int ge = b->grid_e, gn = b->grid_n;
+  auto cg = [&](int stage) -> lh_status {
+    BCgArgs a{b->probs, b->scal, b->items_cg, b->n_items_cg, b->items_n, b->n_items_n, b->n,
+              b->partials, b->active, b->bar, b->status, stage, tol, max_it};
+    BCUDA(b, cudaMemsetAsync(b->bar, 0, 64, s));
+    BCUDA(b, cudaMemsetAsync(b->active, 0, 64, s));
+    void *args[] = {&a};
+    BCUDA(b, cudaLaunchCooperativeKernel((const void *)k_b_cg, dim3(b->grid_cg), dim3(kThreadsCG), args,
+                                         b->smem_cg, s));
+    return LH_OK;
+  };
+  k_b_qdata<<<ge, kThreads, b->smem_e, s>>>(b->q1, b->items_e, b->n_items_e);
+  k_b_force<<<ge, kThreads, b->smem_e, s>>>(b->fa, b->items_e, b->n_items_e);
+  k_b_rhs<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
+  if (lh_status st = cg(0)) return st;
+  k_b_mid<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
+  k_b_force_t<<<ge, kThreads, b->smem_e, s>>>(b->t1, b->items_e, b->n_items_e);
+  k_b_qdata<<<ge, kThreads, b->smem_e, s>>>(b->q2, b->items_e, b->n_items_e);
+  k_b_force<<<ge, kThreads, b->smem_e, s>>>(b->fa, b->items_e, b->n_items_e);
+  k_b_rhs<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
+  if (lh_status st = cg(1)) return st;
+  k_b_final<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
+  k_b_force_t<<<ge, kThreads, b->smem_e, s>>>(b->t2, b->items_e, b->n_items_e);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("batched step launch: ") + cudaGetErrorString(e));
+  return LH_OK;
+}
+
+lh_status lh_batch_step(lh_batch *b, double rel_tol, int max_it, lh_stream_t stream) {
+  if (!b) return LH_ERR_ARG;
+  if (rel_tol <= 0.0) rel_tol = 1e-12;
+  if (max_it <= 0) max_it = 1000;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!b->exec || b->graph_tol != rel_tol || b->graph_max_it != max_it) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    cudaStream_t cap;
+    BCUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    BCUDA(b, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    lh_status st = enqueue_step(b, rel_tol, max_it, cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (st != LH_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (ec != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    b->graph = g;
+    BCUDA(b, cudaGraphInstantiate(&b->exec, g, 0));
+    b->graph_tol = rel_tol;
+    b->graph_max_it = max_it;
+  }
+  BCUDA(b, cudaGraphLaunch(b->exec, s));
+  return LH_OK;
+}
+
+// Times the batched element kernels (stage-1 qdata, F.1, F^T v: none of them
+// changes the state) for tiles of 1, 2 and 4 element batches per work item,
+// one order at a time, and keeps the fastest tile per order. Synchronous.
+lh_status lh_batch_autotune(lh_batch *b, int *tiles_out) {
+  if (!b) return LH_ERR_ARG;
+  cudaEvent_t e0, e1;
+  BCUDA(b, cudaEventCreate(&e0));
+  BCUDA(b, cudaEventCreate(&e1));
+  auto time_kernels = [&]() -> float {
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0);
+      k_b_qdata<<<b->grid_e, kThreads, b->smem_e>>>(b->q1, b->items_e, b->n_items_e);
+      k_b_force<<<b->grid_e, kThreads, b->smem_e>>>(b->fa, b->items_e, b->n_items_e);
+      k_b_force_t<<<b->grid_e, kThreads, b->smem_e>>>(b->t1, b->items_e, b->n_items_e);
+      cudaEventRecord(e1);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  for (int p = 1; p <= 4; ++p) {
+    bool present = false;
+    for (int o : b->order) present |= o == p;
+    if (!present) continue;
+    int best_tile = b->tiles[p];
+    float best_t = 1e30f;
+    for (int tile : {1, 2, 4}) {
+      b->tiles[p] = tile;
+      if (lh_status st = upload_items(b)) return st;
+      const float t = time_kernels();
+      if (t < best_t) { best_t = t; best_tile = tile; }
+    }
+    b->tiles[p] = best_tile;
+    if (lh_status st = upload_items(b)) return st;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  BCUDA(b, cudaGetLastError());
+  if (tiles_out)
+    for (int p = 1; p <= 4; ++p) tiles_out[p - 1] = b->tiles[p];
+  // the captured step graph (if any) holds the old work-list length
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  return LH_OK;
+}
+
+}  // extern "C"

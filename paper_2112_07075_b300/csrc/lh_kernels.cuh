@@ -422,12 +422,11 @@ struct Family {
   static constexpr size_t qdata_smem() {
     return sizeof(double) * (TAB + C2X * ND + QD_S + DIM * C2X * NQ + NB * NQ + NB * NL + RED);
   }
-  static __device__ __forceinline__ void body_qdata(QdataArgs a) {
+  static __device__ __forceinline__ void body_qdata(const QdataArgs &a, int e0) {
     extern __shared__ double sm[];
     double *st = sm, *u = st + TAB, *S = u + C2X * ND, *g = S + QD_S, *eq = g + DIM * C2X * NQ;
     double *el = eq + NB * NQ, *red = el + NB * NL;
     const MeshDesc &m = a.mesh;
-    const int e0 = blockIdx.x * NB;
     const int nb = min(NB, m.ne - e0);
     load_tab(st, a.tab);
     for (int k = threadIdx.x; k < C2X * ND; k += blockDim.x) {
@@ -501,11 +500,10 @@ struct Family {
   static constexpr size_t force_smem() {
     return sizeof(double) * (TAB + DIM * CX * NQ + F_S + CX * ND + NB * NL + NB * NQ);
   }
-  static __device__ __forceinline__ void body_force(ForceArgs a) {
+  static __device__ __forceinline__ void body_force(const ForceArgs &a, int e0) {
     extern __shared__ double sm[];
     double *st = sm, *f = st + TAB, *S = f + DIM * CX * NQ, *y = S + F_S, *ul = y + CX * ND, *uq = ul + NB * NL;
     const MeshDesc &m = a.mesh;
-    const int e0 = blockIdx.x * NB;
     const int nb = min(NB, m.ne - e0);
     load_tab(st, a.tab);
     // D[e][c*DIM+l][q] -> f[l][b*DIM+c][q]  (one contiguous global block per CTA)
@@ -537,12 +535,11 @@ struct Family {
   static constexpr size_t force_t_smem() {
     return sizeof(double) * (TAB + 2 * CX * ND + FT_S + DIM * CX * NQ + CX * NQ + NB * NQ + NB * NL + RED);
   }
-  static __device__ __forceinline__ void body_force_t(ForceTArgs a) {
+  static __device__ __forceinline__ void body_force_t(const ForceTArgs &a, int e0) {
     extern __shared__ double sm[];
     double *st = sm, *u = st + TAB, *xu = u + CX * ND, *S = xu + CX * ND, *g = S + FT_S;
     double *xq = g + DIM * CX * NQ, *sq = xq + CX * NQ, *out = sq + NB * NQ, *red = out + NB * NL;
     const MeshDesc &m = a.mesh;
-    const int e0 = blockIdx.x * NB;
     const int nb = min(NB, m.ne - e0);
     load_tab(st, a.tab);
     gather_elem(u, a.v, DIM, m, e0, nb);
@@ -625,11 +622,10 @@ struct Family {
     __syncthreads();
     interp<DIM, Q, D, CX>(uq, y, S, st + oBt);
   }
-  static __device__ __forceinline__ void body_mass(MassArgs a) {
+  static __device__ __forceinline__ void body_mass(const MassArgs &a, int e0) {
     extern __shared__ double sm[];
     double *st = sm, *u = st + TAB, *S = u + CX * ND, *uq = S + M_S, *y = uq + CX * NQ;
     const MeshDesc &m = a.mesh;
-    const int e0 = blockIdx.x * NB;
     const int nb = min(NB, m.ne - e0);
     load_tab(st, a.tab);
     gather_elem(u, a.x, DIM, m, e0, nb);
@@ -1284,13 +1280,13 @@ struct Family {
 
 // Kernel entry points (free templates; the bodies live in Family).
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_qdata(QdataArgs a) { Family<DIM, P, Q>::body_qdata(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_qdata(QdataArgs a) { Family<DIM, P, Q>::body_qdata(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force(ForceArgs a) { Family<DIM, P, Q>::body_force(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force(ForceArgs a) { Family<DIM, P, Q>::body_force(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force_t(ForceTArgs a) { Family<DIM, P, Q>::body_force_t(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force_t(ForceTArgs a) { Family<DIM, P, Q>::body_force_t(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_mass(MassArgs a) { Family<DIM, P, Q>::body_mass(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_mass(MassArgs a) { Family<DIM, P, Q>::body_mass(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::TC) k_cg(CgArgs a) { Family<DIM, P, Q>::body_cg(a); }
 template <int DIM, int P, int Q>

@@ -75,3 +75,22 @@ def box_vertices(dim: int, n: int, lo: float = 0.0, hi: float = 1.0,
         u = uniform01(seed, ctr.ravel()).reshape(nv, dim)
         V[interior] += (2.0 * u[interior] - 1.0) * jitter * h
     return np.ascontiguousarray(V)
+
+
+def batch_problems(seed: int, count: int = 256, n_lo: int = 8, n_hi: int = 64):
+    """Seeded list of independent 2D problems for the batching workload.
+
+    Problem k gets order p = 1 + floor(4 u0) (uniform in 1..4), mesh size
+    n = n_lo + floor((n_hi - n_lo + 1) u1) (uniform in [n_lo, n_hi]) and kind
+    Taylor-Green for even k, Gresho for odd k (half each), with u0, u1 drawn
+    from uniform01(seed, 2k) and uniform01(seed, 2k + 1).
+    """
+    u = uniform01(seed, np.arange(2 * count, dtype=np.uint64)).reshape(count, 2)
+    out = []
+    for k in range(count):
+        p = 1 + min(3, int(4 * u[k, 0]))
+        n = n_lo + min(n_hi - n_lo, int((n_hi - n_lo + 1) * u[k, 1]))
+        kind = "taylor_green" if k % 2 == 0 else "gresho"
+        lo, hi = (0.0, 1.0) if kind == "taylor_green" else (-0.5, 0.5)
+        out.append(dict(order=p, n=n, kind=kind, lo=lo, hi=hi))
+    return out

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": 0, "fp32_ir": 1}
 
 EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_status", "lh_init_state",
             "lh_update_qdata", "lh_copy_qdata", "lh_force_mult", "lh_force_mult_t", "lh_mass_mult",
-            "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step", "lh_mass_mult_noalloc"]
+            "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step", "lh_mass_mult_noalloc",
+            "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy"]
 
 
 class LhParams(ctypes.Structure):
@@ -80,6 +81,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_energy_solve": (I, [P, VP, VP, VP]),
         "lh_rk2avg_step": (I, [P, VP, VP, VP, D, D, I, VP, VP]),
         "lh_mass_mult_noalloc": (I, [I, I, I, I, I, I, VP, VP, VP, VP]),
+        "lh_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP),
+                                ctypes.POINTER(D), VP, ctypes.POINTER(P)]),
+        "lh_batch_autotune": (I, [P, ctypes.POINTER(I)]),
+        "lh_batch_step": (I, [P, D, I, VP]),
+        "lh_batch_last_error": (ctypes.c_char_p, [P]),
+        "lh_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -235,3 +242,57 @@ class Context:
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))
+
+
+class Batch:
+    """Independent problems advanced together (lh_batch_*): one persistent launch
+    per hot-path operation for all problems, the step replayed as a CUDA graph."""
+
+    def __init__(self, contexts, states, dts):
+        import torch
+        self.lib = load_library()
+        n = len(contexts)
+        self.contexts = list(contexts)
+        self.states = list(states)
+        P = ctypes.c_void_p
+        ctx_arr = (P * n)(*[c.h for c in contexts])
+        xs = (P * n)(*[_ptr(s[0]) for s in states])
+        vs = (P * n)(*[_ptr(s[1]) for s in states])
+        es = (P * n)(*[_ptr(s[2]) for s in states])
+        dt_arr = (ctypes.c_double * n)(*[float(d) for d in dts])
+        raw = np.zeros(n * ctypes.sizeof(LhStepInfo), dtype=np.uint8)
+        self.infos = torch.from_numpy(raw).to(contexts[0].device)
+        h = ctypes.c_void_p()
+        st = self.lib.lh_batch_create(n, ctx_arr, xs, vs, es, dt_arr, _ptr(self.infos), ctypes.byref(h))
+        if st != LH_OK:
+            raise LhError(st, self.lib.lh_last_error(None).decode())
+        self.h = h
+        self.n = n
+
+    def _check(self, st):
+        if st != LH_OK:
+            raise LhError(st, self.lib.lh_batch_last_error(self.h).decode())
+
+    def autotune(self):
+        tiles = (ctypes.c_int * 4)()
+        self._check(self.lib.lh_batch_autotune(self.h, tiles))
+        return list(tiles)
+
+    def step(self, rel_tol=1e-12, max_it=1000):
+        self._check(self.lib.lh_batch_step(self.h, float(rel_tol), int(max_it), _stream()))
+
+    def read_infos(self):
+        raw = self.infos.cpu().numpy().tobytes()
+        sz = ctypes.sizeof(LhStepInfo)
+        return [LhStepInfo.from_buffer_copy(raw[i * sz:(i + 1) * sz]) for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lh_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+"""Batching form: every problem of a batch matches its own unbatched run and the oracle.
+
+The batched step runs the same per-problem arithmetic as lh_rk2avg_step with a
+fixed dt except for the summation order of the CG dot products, so each problem
+must agree with its unbatched run to 1e-12 relative per field, and with the FP64
+oracle to the 1e-11 parity bar.
+"""
+import numpy as np
+import pytest
+
+from oracle.hydro import Hydro, Params
+from paper_2112_07075_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _problems():
+    # every order, both kinds, uneven sizes
+    return [dict(order=p, n=n, kind=k) for p, n, k in
+            [(1, 6, "taylor_green"), (2, 5, "gresho"), (3, 4, "taylor_green"), (4, 3, "gresho"),
+             (2, 7, "taylor_green"), (1, 9, "gresho"), (4, 2, "taylor_green"), (3, 5, "gresho")]]
+
+
+def _make(pr):
+    from paper_2112_07075_b300.lh import Context
+    lo, hi = (0.0, 1.0) if pr["kind"] == "taylor_green" else (-0.5, 0.5)
+    V = inputs.box_vertices(2, pr["n"], lo, hi)
+    src = "tg2d" if pr["kind"] == "taylor_green" else "none"
+    ctx = Context(2, pr["n"], V, pr["order"], 2 * pr["order"], source=src)
+    return ctx, V, src
+
+
+def test_batched_steps_match_unbatched_and_oracle():
+    from paper_2112_07075_b300.lh import Batch
+    probs = _problems()
+    steps, dt = 4, 5e-4
+    ctxs, states, refs = [], [], []
+    for pr in probs:
+        ctx, V, src = _make(pr)
+        ctxs.append(ctx)
+        states.append(ctx.init_state(pr["kind"]))
+        # unbatched reference with its own context
+        rctx, _, _ = _make(pr)
+        x, v, e = rctx.init_state(pr["kind"])
+        info = rctx.new_step_info()
+        for _ in range(steps):
+            rctx.rk2avg_step(x, v, e, dt, info)
+        refs.append((x, v, e, rctx))
+    batch = Batch(ctxs, states, [dt] * len(ctxs))
+    tiles = batch.autotune()
+    assert all(t in (1, 2, 4) for t in tiles)
+    for _ in range(steps):
+        batch.step()
+    torch.cuda.synchronize()
+    infos = batch.read_infos()
+    for i, pr in enumerate(probs):
+        assert infos[i].steps == steps and infos[i].status == 0
+        assert min(infos[i].cg_iters) > 0 and max(infos[i].cg_rel_res) <= 1e-12
+        for a, b in zip(states[i], refs[i][:3]):
+            a, b = a.cpu().numpy(), b.cpu().numpy()
+            assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b), (i, pr)
+    # oracle for two problems (one per kind)
+    for i in (2, 3):
+        pr = probs[i]
+        lo, hi = (0.0, 1.0) if pr["kind"] == "taylor_green" else (-0.5, 0.5)
+        hy = Hydro(Params(dim=2, n=pr["n"], order=pr["order"], q1=2 * pr["order"],
+                          vertices=inputs.box_vertices(2, pr["n"], lo, hi),
+                          source="tg2d" if pr["kind"] == "taylor_green" else "none"))
+        xo, vo, eo = hy.initial_state(pr["kind"])
+        for _ in range(steps):
+            xo, vo, eo, _ = hy.rk2avg_step(xo, vo, eo, dt=dt)
+        for a, b in zip(states[i], (xo, vo, eo)):
+            a = a.cpu().numpy()
+            assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b)
+    batch.close()
