@@ -252,6 +252,55 @@ const char *lh_batch_last_error(const lh_batch *b);
 /* Release the batch (not its contexts). NULL is accepted. */
 void lh_batch_destroy(lh_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Learned form: a small per-element MLP predicts the initial guess of the
+ * velocity mass solves of lh_rk2avg_step. Network: 586 -> 128 -> 128 -> 192,
+ * GELU (erf) after both hidden layers, BF16 weights and activations on the
+ * tensor cores with FP32 accumulation, FP32 master weights, Adam (0.9, 0.999,
+ * 1e-8), mean-squared-error loss. Inputs per element (3D Q3): the three most
+ * recent mass-solve solutions at its 64 nodes divided by the RMS s of the latest
+ * one (576 values, most recent first), its Jacobian at the centroid divided by
+ * h0*p (9) and det J / (h0*p)^3 (1). Output: (a_new - a_latest) / s at its nodes.
+ * Parameters are one flat FP32 vector: W1 [128][592] (input padded to 592;
+ * columns 586..591 stay zero), b1[128], W2 [128][128], b2[128], W3 [192][128], b3[192].
+ * ------------------------------------------------------------------------- */
+typedef struct lh_mlp lh_mlp;
+
+/* Create an MLP for batches of up to max_rows elements; weights uniform in
+ * +-sqrt(6 / fan_in) from `seed`, biases zero. Allocates its device buffers. */
+lh_status lh_mlp_create(unsigned long long seed, int max_rows, lh_mlp **out);
+void lh_mlp_destroy(lh_mlp *m);
+/* Number of FP32 parameters. */
+int lh_mlp_num_params(void);
+/* Copy the FP32 parameters to / from HOST memory (set also resets Adam). Synchronous. */
+lh_status lh_mlp_get_params(const lh_mlp *m, float *host_out);
+lh_status lh_mlp_set_params(lh_mlp *m, const float *host_in);
+/* Y[n][192] = MLP(X[n][586]); X, Y DEVICE FP32. */
+lh_status lh_mlp_forward(lh_mlp *m, const float *X, int n, float *Y, lh_stream_t stream);
+/* Loss (mean over n*192 outputs of (Y - T)^2, one DEVICE float) and, if grads is
+ * not NULL, its gradient (DEVICE FP32, lh_mlp_num_params() values); no update. */
+lh_status lh_mlp_gradients(lh_mlp *m, const float *X, const float *T, int n, float *grads, float *loss,
+                           lh_stream_t stream);
+/* One Adam step with learning rate lr on the batch (X, T); loss as above. */
+lh_status lh_mlp_train_step(lh_mlp *m, const float *X, const float *T, int n, float lr, float *loss,
+                            lh_stream_t stream);
+const char *lh_mlp_last_error(const lh_mlp *m);
+
+/* Attach the learned form to a context (3D, order 3, q1 = 6). mode 1: record a
+ * training example per element at every mass solve of lh_rk2avg_step that has
+ * three earlier solutions (features into X_buf[row][586], targets into
+ * T_buf[row][192], DEVICE, until capacity_rows rows are filled). mode 2: predict
+ * the initial guess with `mlp` (context precision must be LH_PRECISION_FP32_IR):
+ * the guess g and the previous solution are compared by ||b - M .||_2 (FP32
+ * mass action, FP64 sums) and the smaller starts CG; CG still runs to its
+ * tolerance. mode 0: detach. Allocates the form's device buffers (a set-up
+ * call); synchronous. */
+lh_status lh_learn_attach(lh_ctx *ctx, lh_mlp *mlp, int mode, float *X_buf, float *T_buf, int capacity_rows);
+/* HOST counters of the attached learned form: rows recorded, mass solves seen,
+ * predictions made, predictions that won the residual comparison (the last
+ * one reads device memory; synchronous). Any pointer may be NULL. */
+lh_status lh_learn_stats(const lh_ctx *ctx, int *rows_recorded, int *solves, int *predictions, int *learned_used);
+
 /* Mass product without any device allocation (the paper has no counterpart; this
  * is a convenience of this library). Computes the same y = M_v x as lh_mass_mult,
  * but takes everything from the caller and needs no context, so nothing is

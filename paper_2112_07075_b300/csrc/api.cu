@@ -191,6 +191,7 @@ extern "C" {
 
 void lh_destroy(lh_ctx *ctx) {
   if (!ctx) return;
+  lh::learn_free(ctx->learn);
   if (ctx->arena) cudaFree(ctx->arena);
   delete ctx;
 }
@@ -582,9 +583,11 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
   o.qdata(qa, c->grid_elem, s);
   if (lh_status st = check_launch(c, "qdata 1")) return st;
   if (lh_status st = force_impl(c, nullptr, c->rhs, -1.0, c->invdiag, s)) return st;
+  if (lh_status st = lh::learn_before_solve(c, x, s)) return st;
   if (lh_status st = cg_impl(c, c->rhs, c->a_prev, rel_tol, max_it, nullptr, &info->cg_iters[0],
                              &info->cg_rel_res[0], s))
     return st;
+  if (lh_status st = lh::learn_after_solve(c, s)) return st;
   k_rk_mid<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x, v, c->a_prev, dtp, c->xh, c->vh);
   if (lh_status st = check_launch(c, "rk mid")) return st;
   ForceTArgs fa{};
@@ -606,9 +609,11 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
   o.qdata(qa, c->grid_elem, s);
   if (lh_status st = check_launch(c, "qdata 2")) return st;
   if (lh_status st = force_impl(c, nullptr, c->rhs, -1.0, c->invdiag, s)) return st;
+  if (lh_status st = lh::learn_before_solve(c, c->xh, s)) return st;
   if (lh_status st = cg_impl(c, c->rhs, c->a_prev, rel_tol, max_it, nullptr, &info->cg_iters[1],
                              &info->cg_rel_res[1], s))
     return st;
+  if (lh_status st = lh::learn_after_solve(c, s)) return st;
   k_rk_final<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x, v, c->a_prev, dtp, c->vb);
   if (lh_status st = check_launch(c, "rk final")) return st;
   fa.v = c->vb;

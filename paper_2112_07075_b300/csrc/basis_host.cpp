@@ -85,6 +85,15 @@ static double lagrange_d(const double *z, int n, int i, double x) {
   return s;
 }
 
+void h1_basis_at(int p, double x, double *vals, double *ders) {
+  double z[5];
+  gll_nodes(p, z);
+  for (int i = 0; i <= p; ++i) {
+    vals[i] = lagrange(z, p + 1, i, x);
+    ders[i] = lagrange_d(z, p + 1, i, x);
+  }
+}
+
 int table_length(int p, int q1) {
   const int D = p + 1, Q = q1, L = p;
   return 5 * Q * D + 2 * Q * L + 2 * Q + D;

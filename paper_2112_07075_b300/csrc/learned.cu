@@ -1,0 +1,387 @@
+// Learned form: a per-element MLP (mlp.cu) predicts the initial guess of the
+// velocity mass solve from the three most recent mass-solve solutions and the
+// element's Jacobian at its centroid. Supported for 3D Q3 (64 nodes x 3
+// components = 192 outputs per element) with q1 = 6.
+//
+// Per solve of lh_rk2avg_step, with s = RMS of the latest solution a_1 over the
+// free DOFs:
+//   features  X_e = [a_1, a_2, a_3 at the element's nodes] / s (576 values, most
+//             recent first) ++ [J(centroid) / (h0 p), det J / (h0 p)^3] (10 values)
+//   target    T_e = (a_new - a_1) / s at the element's nodes (recording mode)
+//   guess     g = a_1 + s * (average over the elements sharing each node of the
+//             MLP output), zero on constrained DOFs (prediction mode)
+// In prediction mode the residuals ||b - M g|| and ||b - M a_1|| are compared
+// (FP32 mass action, FP64 sums) and the smaller one's vector starts CG; the CG
+// tolerance is unchanged, so the guess only changes the iteration count.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "lh_kernels.cuh"
+#include "lh_mlp.h"
+
+using namespace lh;
+using namespace lh::mlp;
+
+extern "C" lh_status lh_mlp_forward(lh_mlp *m, const float *X, int n, float *Y, lh_stream_t stream);
+
+namespace lh {
+namespace learn {
+namespace {
+
+using F = Family<3, 3, 6>;
+constexpr int D = 4, ND = 64;
+constexpr int kBlocks = 592;
+
+struct Cent { double v[4], d[4]; };   // 1D basis values / derivatives at the centre 0.5
+
+__global__ void k_sumsq(size_t nv, const double *__restrict__ a, const double *__restrict__ idg,
+                        double *__restrict__ part) {
+  double acc = 0.0, cnt = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (size_t)gridDim.x * blockDim.x)
+    if (idg[k] != 0.0) { acc = fma(a[k], a[k], acc); cnt += 1.0; }
+  double v[2] = {acc, cnt};
+  __shared__ double red[64];
+  block_sum<2>(v, red);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = v[0]; part[2 * blockIdx.x + 1] = v[1]; }
+}
+__global__ void k_scale_final(int nb, const double *__restrict__ part, double *__restrict__ s) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) { a += part[2 * i]; c += part[2 * i + 1]; }
+    a = warp_sum(a);
+    c = warp_sum(c);
+    if (threadIdx.x == 0) {
+      const double rms = c > 0.0 ? sqrt(a / c) : 0.0;
+      *s = rms > 0.0 ? rms : 1.0;
+    }
+  }
+}
+
+// History features: X[row0 + e][k*192 + c*64 + i] = hist_k[c][node(e,i)] / s.
+__global__ void k_hist_features(MeshDesc m, const double *__restrict__ h0, const double *__restrict__ h1,
+                                const double *__restrict__ h2, const double *__restrict__ s, float *__restrict__ X) {
+  const size_t total = (size_t)m.ne * 576;
+  const double is = 1.0 / *s;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int e = (int)(t / 576), f = (int)(t % 576);
+    const int k = f / 192, c = (f / 64) % 3, i = f % 64;
+    const double *h = k == 0 ? h0 : (k == 1 ? h1 : h2);
+    const int g = h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
+    X[(size_t)e * kIn + f] = (float)(h[(size_t)c * m.nh1 + g] * is);
+  }
+}
+
+// Jacobian features at the element centroid: 9 entries of J / (h0 p) and det J / (h0 p)^3.
+__global__ void k_jac_features(MeshDesc m, const double *__restrict__ x, Cent cb, double hs,
+                               float *__restrict__ X) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.ne; e += gridDim.x * blockDim.x) {
+    const int base = h1_base<3, D>(m, e);
+    double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < ND; ++i) {
+      const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
+      const double gx = cb.d[ix] * cb.v[iy] * cb.v[iz];
+      const double gy = cb.v[ix] * cb.d[iy] * cb.v[iz];
+      const double gz = cb.v[ix] * cb.v[iy] * cb.d[iz];
+      const int g = base + h1_local<3, D>(m, i);
+      for (int c = 0; c < 3; ++c) {
+        const double xc = x[(size_t)c * m.nh1 + g];
+        J[c * 3 + 0] += xc * gx;
+        J[c * 3 + 1] += xc * gy;
+        J[c * 3 + 2] += xc * gz;
+      }
+    }
+    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    float *out = X + (size_t)e * kIn + 576;
+    for (int k = 0; k < 9; ++k) out[k] = (float)(J[k] / hs);
+    out[9] = (float)(det / (hs * hs * hs));
+  }
+}
+
+// Targets: T[row0 + e][c*64 + i] = (a_new - a_1)[c][node(e,i)] / s.
+__global__ void k_targets(MeshDesc m, const double *__restrict__ anew, const double *__restrict__ a1,
+                          const double *__restrict__ s, float *__restrict__ T) {
+  const size_t total = (size_t)m.ne * kOut;
+  const double is = 1.0 / *s;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int e = (int)(t / kOut), f = (int)(t % kOut);
+    const int c = f / 64, i = f % 64;
+    const size_t k = (size_t)c * m.nh1 + h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
+    T[t] = (float)((anew[k] - a1[k]) * is);
+  }
+}
+
+// Guess at nodes: g = a_1 + s * mean over element copies of the MLP output; 0 on constrained DOFs.
+__global__ void k_assemble(MeshDesc m, const float *__restrict__ Y, const double *__restrict__ a1,
+                           const double *__restrict__ s, const double *__restrict__ idg, double *__restrict__ g) {
+  const double sc = *s;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < m.nh1; n += gridDim.x * blockDim.x) {
+    int off[8];
+    const int cnt = node_copies<3, D>(m, n, 3, off);
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * m.nh1 + n;
+      double sum = 0.0;
+      for (int j = 0; j < cnt; ++j) sum += (double)Y[off[j] + c * ND];
+      g[k] = idg[k] != 0.0 ? fma(sc, sum / cnt, a1[k]) : 0.0;
+    }
+  }
+}
+
+// FP32 E-vectors of M g (evA) and M a_1 (evB) for the residual comparison.
+__global__ void __launch_bounds__(F::THREADS) k_resid_elem(MeshDesc m, const double *__restrict__ tab,
+                                                           const float *__restrict__ mq32, const double *__restrict__ g,
+                                                           const double *__restrict__ a1, const double *__restrict__ idg,
+                                                           float *__restrict__ evA, float *__restrict__ evB) {
+  constexpr int CX = F::CX, NQ = F::NQ, Q = 6;
+  constexpr int MS = F::M_S;
+  extern __shared__ double smd[];
+  float *tb = (float *)smd, *tbt = tb + Q * D, *u = tbt + Q * D, *S = u + CX * ND, *uq = S + MS, *y = uq + CX * NQ;
+  for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x) tb[k] = (float)tab[k < Q * D ? F::oB + k : F::oBt + k - Q * D];
+  const int e0 = blockIdx.x * F::NB, nb = min(F::NB, m.ne - e0);
+  for (int pass = 0; pass < 2; ++pass) {
+    const double *src = pass == 0 ? g : a1;
+    float *ev = pass == 0 ? evA : evB;
+    __syncthreads();
+    for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+      const int i = k % ND, bc = k / ND, c = bc % 3, b = bc / 3;
+      float val = 0.0f;
+      if (b < nb) {
+        const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e0 + b) + h1_local<3, D>(m, i);
+        val = idg[gi] != 0.0 ? (float)src[gi] : 0.0f;
+      }
+      u[k] = val;
+    }
+    __syncthreads();
+    interp<3, D, Q, CX>(u, uq, S, tb);
+    for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
+      const int q = k % NQ, b = (k / NQ) / 3;
+      uq[k] *= b < nb ? mq32[(size_t)(e0 + b) * NQ + q] : 0.0f;
+    }
+    __syncthreads();
+    interp<3, Q, D, CX>(uq, y, S, tbt);
+    for (int k = threadIdx.x; k < nb * 3 * ND; k += blockDim.x) ev[(size_t)e0 * 3 * ND + k] = y[k];
+  }
+}
+
+// Residual norms of both candidates: per-block partials (FP64 sums of FP32 residuals).
+__global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const double *__restrict__ idg,
+                              const float *__restrict__ evA, const float *__restrict__ evB, double *__restrict__ part) {
+  double acc[2] = {0.0, 0.0};
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < m.nh1; n += gridDim.x * blockDim.x) {
+    int off[8];
+    const int cnt = node_copies<3, D>(m, n, 3, off);
+    for (int c = 0; c < 3; ++c) {
+      const size_t k = (size_t)c * m.nh1 + n;
+      if (idg[k] == 0.0) continue;
+      float ma = 0.0f, mb = 0.0f;
+      for (int j = 0; j < cnt; ++j) { ma += evA[off[j] + c * ND]; mb += evB[off[j] + c * ND]; }
+      const double ra = b[k] - (double)ma, rb = b[k] - (double)mb;
+      acc[0] = fma(ra, ra, acc[0]);
+      acc[1] = fma(rb, rb, acc[1]);
+    }
+  }
+  __shared__ double red[64];
+  block_sum<2>(acc, red);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = acc[0]; part[2 * blockIdx.x + 1] = acc[1]; }
+}
+
+// Decide (one warp) and count: flag = ||b - M g|| < ||b - M a_1||.
+__global__ void k_decide(int nb, const double *__restrict__ part, int *__restrict__ flag, int *__restrict__ used,
+                         double *__restrict__ ratio) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) { a += part[2 * i]; b += part[2 * i + 1]; }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) {
+      const int f = a < b ? 1 : 0;
+      *flag = f;
+      *used += f;
+      *ratio = b > 0.0 ? sqrt(a / b) : 1.0;
+    }
+  }
+}
+
+__global__ void k_apply(size_t nv, const int *__restrict__ flag, const double *__restrict__ g, double *__restrict__ a) {
+  if (!*flag) return;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (size_t)gridDim.x * blockDim.x)
+    a[k] = g[k];
+}
+
+}  // namespace
+}  // namespace learn
+}  // namespace lh
+
+struct lh_learn {
+  lh_mlp *mlp = nullptr;
+  int mode = 0;              // 1 record, 2 predict
+  char *arena = nullptr;
+  double *hist[3] = {nullptr, nullptr, nullptr};
+  int count = 0, head = 0;   // solutions stored, next ring slot
+  float *X = nullptr, *Y = nullptr, *evB = nullptr, *evA32 = nullptr;
+  double *guess = nullptr, *scale = nullptr, *part = nullptr, *ratio = nullptr;
+  int *flag = nullptr, *used = nullptr;
+  float *dX = nullptr, *dT = nullptr;
+  int capacity = 0, rows = 0, solves = 0, predicted = 0;
+  bool pending = false;      // features of the current solve were recorded
+  size_t smem_resid = 0;
+  learn::Cent cent{};
+  double hs = 1.0;
+};
+
+namespace lh {
+
+static const double *hist_at(lh_learn *L, int age) {   // age 0 = most recent
+  return L->hist[(L->head + 2 - age + 3) % 3];
+}
+
+// Before a mass solve of lh_rk2avg_step (positions x of the stage, rhs in c->rhs).
+lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
+  lh_learn *L = c->learn;
+  if (!L || L->mode == 0 || L->count < 3) return LH_OK;
+  using namespace learn;
+  const MeshDesc &m = c->mesh;
+  const size_t nv = c->nv;
+  const double *a1 = hist_at(L, 0);
+  k_sumsq<<<kBlocks, 256, 0, s>>>(nv, a1, c->invdiag, L->part);
+  k_scale_final<<<1, 32, 0, s>>>(kBlocks, L->part, L->scale);
+  float *X = L->X;
+  L->pending = false;
+  if (L->mode == 1) {
+    if (L->rows + m.ne > L->capacity) return LH_OK;
+    X = L->dX + (size_t)L->rows * kIn;
+    L->pending = true;
+  }
+  k_hist_features<<<4 * kBlocks, 256, 0, s>>>(m, a1, hist_at(L, 1), hist_at(L, 2), L->scale, X);
+  k_jac_features<<<(m.ne + 255) / 256, 256, 0, s>>>(m, x, L->cent, L->hs, X);
+  if (L->mode == 2) {
+    if (lh_status st = lh_mlp_forward(L->mlp, X, m.ne, L->Y, (lh_stream_t)s)) return st;
+    k_assemble<<<2 * kBlocks, 256, 0, s>>>(m, L->Y, a1, L->scale, c->invdiag, L->guess);
+    k_resid_elem<<<c->grid_elem, F::THREADS, L->smem_resid, s>>>(
+        m, c->tab, c->mq32, L->guess, a1, c->invdiag, L->evA32, L->evB);
+    k_resid_nodes<<<kBlocks, 256, 0, s>>>(m, c->rhs, c->invdiag, L->evA32, L->evB, L->part);
+    k_decide<<<1, 32, 0, s>>>(kBlocks, L->part, L->flag, L->used, L->ratio);
+    k_apply<<<kBlocks, 256, 0, s>>>(nv, L->flag, L->guess, c->a_prev);
+    L->predicted += 1;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->err = std::string("learned guess: ") + cudaGetErrorString(e);
+    return LH_ERR_CUDA;
+  }
+  return LH_OK;
+}
+
+// After a mass solve: record the target (recording mode) and push the solution into the history.
+lh_status learn_after_solve(lh_ctx *c, cudaStream_t s) {
+  lh_learn *L = c->learn;
+  if (!L || L->mode == 0) return LH_OK;
+  using namespace learn;
+  if (L->mode == 1 && L->pending) {
+    k_targets<<<4 * kBlocks, 256, 0, s>>>(c->mesh, c->a_prev, hist_at(L, 0), L->scale,
+                                          L->dT + (size_t)L->rows * kOut);
+    L->rows += c->mesh.ne;
+    L->pending = false;
+  }
+  cudaMemcpyAsync(L->hist[L->head], c->a_prev, c->nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  L->head = (L->head + 1) % 3;
+  L->count = L->count < 3 ? L->count + 1 : 3;
+  L->solves += 1;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->err = std::string("learned history: ") + cudaGetErrorString(e);
+    return LH_ERR_CUDA;
+  }
+  return LH_OK;
+}
+
+void learn_free(lh_learn *L) {
+  if (!L) return;
+  if (L->arena) cudaFree(L->arena);
+  delete L;
+}
+
+}  // namespace lh
+
+extern "C" {
+
+lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float *T_buf, int capacity_rows) {
+  if (!c) return LH_ERR_ARG;
+  if (mode == 0) {
+    learn_free(c->learn);
+    c->learn = nullptr;
+    return LH_OK;
+  }
+  if (c->dim != 3 || c->p != 3 || c->q1 != 6) {
+    c->err = "the learned guess is defined for 3D Q3 with q1 = 6";
+    return LH_ERR_UNSUPPORTED;
+  }
+  if (mode == 1 && (!X_buf || !T_buf || capacity_rows < 1)) {
+    c->err = "recording needs example buffers";
+    return LH_ERR_ARG;
+  }
+  if (mode == 2 && (!mlp || c->prm.precision != LH_PRECISION_FP32_IR)) {
+    c->err = "prediction needs an MLP and a context with LH_PRECISION_FP32_IR";
+    return LH_ERR_ARG;
+  }
+  if (mode != 1 && mode != 2) { c->err = "mode must be 0, 1 or 2"; return LH_ERR_ARG; }
+  learn_free(c->learn);
+  c->learn = nullptr;
+  lh_learn *L = new lh_learn();
+  L->mlp = mlp;
+  L->mode = mode;
+  L->dX = X_buf;
+  L->dT = T_buf;
+  L->capacity = capacity_rows;
+  const size_t nv = c->nv, ne = c->mesh.ne;
+  const size_t bytes_list[] = {3 * nv * 8, ne * lh::mlp::kIn * 4, ne * lh::mlp::kOut * 4, ne * 3 * 64 * 4,
+                               ne * 3 * 64 * 4, nv * 8, 4 * 1184 * 8 + 1024};
+  size_t bytes = 0;
+  for (size_t b : bytes_list) bytes += (b + 255) / 256 * 256;
+  if (cudaMalloc(&L->arena, bytes) != cudaSuccess) {
+    delete L;
+    c->err = "learned-form buffers could not be allocated";
+    return LH_ERR_OOM;
+  }
+  cudaMemset(L->arena, 0, bytes);
+  char *p = L->arena;
+  auto take = [&](size_t b) { char *q = p; p += (b + 255) / 256 * 256; return q; };
+  double *h = (double *)take(bytes_list[0]);
+  for (int k = 0; k < 3; ++k) L->hist[k] = h + k * nv;
+  L->X = (float *)take(bytes_list[1]);
+  L->Y = (float *)take(bytes_list[2]);
+  L->evA32 = (float *)take(bytes_list[3]);
+  L->evB = (float *)take(bytes_list[4]);
+  L->guess = (double *)take(bytes_list[5]);
+  char *misc = take(bytes_list[6]);
+  L->part = (double *)misc;
+  L->scale = (double *)(misc + 4 * 1184 * 8);
+  L->ratio = L->scale + 1;
+  L->flag = (int *)(L->scale + 2);
+  L->used = L->flag + 1;
+  lh::h1_basis_at(3, 0.5, L->cent.v, L->cent.d);
+  L->hs = c->h0 * c->p;
+  const size_t smem = sizeof(float) * (2 * 6 * 4 + lh::learn::F::CX * 64 + lh::learn::F::M_S +
+                                       lh::learn::F::CX * lh::learn::F::NQ + lh::learn::F::CX * 64) + 16;
+  cudaFuncSetAttribute((const void *)lh::learn::k_resid_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  L->smem_resid = smem;
+  c->learn = L;
+  return cudaDeviceSynchronize() == cudaSuccess ? LH_OK : LH_ERR_CUDA;
+}
+
+lh_status lh_learn_stats(const lh_ctx *c, int *rows_recorded, int *solves, int *predictions, int *learned_used) {
+  if (!c || !c->learn) return LH_ERR_ARG;
+  const lh_learn *L = c->learn;
+  if (rows_recorded) *rows_recorded = L->rows;
+  if (solves) *solves = L->solves;
+  if (predictions) *predictions = L->predicted;
+  if (learned_used) {
+    if (cudaMemcpy(learned_used, L->used, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LH_ERR_CUDA;
+  }
+  return LH_OK;
+}
+
+}  // extern "C"

@@ -145,10 +145,20 @@ const Ops *find_ops_3d(int p, int q1);
 void build_tables(int p, int q1, double *tab, int tab_len);
 int table_length(int p, int q1);
 void gll_nodes(int p, double *z);
+// H1 (GLL-node) basis values and derivatives of order p at the reference point x.
+void h1_basis_at(int p, double x, double *vals, double *ders);
 
 // Sets the message lh_last_error(NULL) returns (calls without a context).
 void set_global_error(const std::string &msg);
 
+}  // namespace lh
+
+struct lh_learn;
+namespace lh {
+// Learned-form hooks around each mass solve of lh_rk2avg_step (learned.cu).
+lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s);
+lh_status learn_after_solve(lh_ctx *c, cudaStream_t s);
+void learn_free(lh_learn *L);
 }  // namespace lh
 
 // The context behind the opaque lh_ctx handle (one problem: mesh, tables, arena).
@@ -173,6 +183,7 @@ struct lh_ctx {
   unsigned int *counter = nullptr;
   void *bar = nullptr;   // lh::GridBarrier
   int *dstatus = nullptr;
+  lh_learn *learn = nullptr;   // learned-form state (lh_learn_attach), or NULL
   std::string err = "no error";
 };
 

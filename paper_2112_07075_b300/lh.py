@@ -26,7 +26,10 @@ PRECISIONS = {"fp64": 0, "fp32_ir": 1}
 EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_status", "lh_init_state",
             "lh_update_qdata", "lh_copy_qdata", "lh_force_mult", "lh_force_mult_t", "lh_mass_mult",
             "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step", "lh_mass_mult_noalloc",
-            "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy"]
+            "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy",
+            "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
+            "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_learn_attach",
+            "lh_learn_stats"]
 
 
 class LhParams(ctypes.Structure):
@@ -87,6 +90,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_batch_step": (I, [P, D, I, VP]),
         "lh_batch_last_error": (ctypes.c_char_p, [P]),
         "lh_batch_destroy": (None, [P]),
+        "lh_mlp_create": (I, [ctypes.c_ulonglong, I, ctypes.POINTER(P)]),
+        "lh_mlp_destroy": (None, [P]),
+        "lh_mlp_num_params": (I, []),
+        "lh_mlp_get_params": (I, [P, VP]),
+        "lh_mlp_set_params": (I, [P, VP]),
+        "lh_mlp_forward": (I, [P, VP, I, VP, VP]),
+        "lh_mlp_gradients": (I, [P, VP, VP, I, VP, VP, VP]),
+        "lh_mlp_train_step": (I, [P, VP, VP, I, ctypes.c_float, VP, VP]),
+        "lh_mlp_last_error": (ctypes.c_char_p, [P]),
+        "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
+        "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -296,3 +310,73 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+MLP_IN, MLP_IN_PAD, MLP_HID, MLP_OUT = 586, 592, 128, 192
+
+
+class MLP:
+    """The learned-form per-element MLP (lh_mlp_*); training and inference run in liblh's kernels."""
+
+    def __init__(self, seed=0, max_rows=1 << 17):
+        import torch
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.lh_mlp_create(int(seed), int(max_rows), ctypes.byref(h))
+        if st != LH_OK:
+            raise LhError(st, self.lib.lh_last_error(None).decode())
+        self.h = h
+        self.max_rows = max_rows
+        self.nparams = self.lib.lh_mlp_num_params()
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def _check(self, st):
+        if st != LH_OK:
+            raise LhError(st, self.lib.lh_mlp_last_error(self.h).decode())
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        self._check(self.lib.lh_mlp_get_params(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.nparams
+        self._check(self.lib.lh_mlp_set_params(self.h, w.ctypes.data_as(ctypes.c_void_p)))
+
+    def forward(self, X, Y):
+        self._check(self.lib.lh_mlp_forward(self.h, _ptr(X), int(X.shape[0]), _ptr(Y), _stream()))
+
+    def gradients(self, X, T, grads=None):
+        self._check(self.lib.lh_mlp_gradients(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grads),
+                                              _ptr(self.loss), _stream()))
+        return self.loss
+
+    def train_step(self, X, T, lr):
+        self._check(self.lib.lh_mlp_train_step(self.h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
+                                               _ptr(self.loss), _stream()))
+        return self.loss
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lh_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def learn_attach(ctx, mlp, mode, X_buf=None, T_buf=None):
+    """Attach the learned form to a context: mode 1 records (X_buf, T_buf rows), 2 predicts, 0 detaches."""
+    cap = 0 if X_buf is None else int(X_buf.shape[0])
+    ctx._check(ctx.lib.lh_learn_attach(ctx.h, mlp.h if mlp is not None else None, int(mode), _ptr(X_buf),
+                                       _ptr(T_buf), cap))
+
+
+def learn_stats(ctx):
+    vals = [ctypes.c_int() for _ in range(4)]
+    ctx._check(ctx.lib.lh_learn_stats(ctx.h, *[ctypes.byref(v) for v in vals]))
+    return dict(rows=vals[0].value, solves=vals[1].value, predictions=vals[2].value, used=vals[3].value)

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "lh.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:lh_status|void|const char \*)\s*\*?\s*(lh_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:lh_status|void|int|const char \*)\s*\*?\s*(lh_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_binding_names():

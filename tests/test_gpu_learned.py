@@ -1,0 +1,105 @@
+"""Learned form: the GPU MLP against its CPU reference, training, and the guess in the step.
+
+Gradients are compared per parameter tensor with the CPU reference that rounds to
+bfloat16 at the same points as the GPU kernels (tolerance 2e-3 relative in the
+Frobenius norm: the GPU accumulates in FP32, the reference in FP64, which can flip
+a bfloat16 rounding). The learned guess only changes where CG starts, so a run
+with it must give the same state as the run without it within the precision
+form's 1e-10 bar, and the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from oracle.hydro import Hydro, Params
+from paper_2112_07075_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _tensors(g):
+    return {"W1": g[ref.OFF_W1:ref.OFF_B1], "b1": g[ref.OFF_B1:ref.OFF_W2], "W2": g[ref.OFF_W2:ref.OFF_B2],
+            "b2": g[ref.OFF_B2:ref.OFF_W3], "W3": g[ref.OFF_W3:ref.OFF_B3], "b3": g[ref.OFF_B3:]}
+
+
+def _data(n, seed):
+    X = inputs.uniform(seed, (n, ref.IN), -1.0, 1.0)
+    T = inputs.uniform(seed + 1, (n, ref.OUT), -0.5, 0.5)
+    return X, T
+
+
+def test_forward_and_gradients_match_bf16_reference():
+    from paper_2112_07075_b300.lh import MLP
+    net = MLP(seed=5, max_rows=4096)
+    w = net.get_params().astype(np.float64)
+    assert np.all(w.reshape(-1)[ref.OFF_W1:ref.OFF_B1].reshape(ref.HID, ref.IN_PAD)[:, ref.IN:] == 0)
+    X, T = _data(300, 11)
+    Xg = torch.from_numpy(X.astype(np.float32)).cuda()
+    Tg = torch.from_numpy(T.astype(np.float32)).cuda()
+    Y = torch.zeros((300, ref.OUT), dtype=torch.float32, device="cuda")
+    net.forward(Xg, Y)
+    Yr, _ = ref.forward(w, X, bf16=True)
+    assert np.linalg.norm(Y.cpu().numpy() - Yr) <= 1e-3 * np.linalg.norm(Yr)
+    g = torch.zeros(net.nparams, dtype=torch.float32, device="cuda")
+    loss = float(net.gradients(Xg, Tg, g).item())
+    lr, gr = ref.grads(w, X, T, bf16=True)
+    assert abs(loss - lr) <= 1e-4 * lr
+    gg = g.cpu().numpy().astype(np.float64)
+    for name, (a, b) in {k: (_tensors(gg)[k], v) for k, v in _tensors(gr).items()}.items():
+        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b), name
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    from paper_2112_07075_b300.lh import MLP
+    net = MLP(seed=1, max_rows=2048)
+    X, _ = _data(2048, 21)
+    # a learnable target: a fixed linear map of the first 192 inputs
+    T = 0.5 * X[:, :ref.OUT] - 0.25 * X[:, ref.OUT:2 * ref.OUT]
+    Xg = torch.from_numpy(X.astype(np.float32)).cuda()
+    Tg = torch.from_numpy(T.astype(np.float32)).cuda()
+    first = float(net.gradients(Xg, Tg).item())
+    for _ in range(300):
+        net.train_step(Xg, Tg, 2e-3)
+    last = float(net.gradients(Xg, Tg).item())
+    assert last < 0.2 * first, (first, last)
+    net.close()
+
+
+def test_learned_guess_keeps_the_solution_and_is_used():
+    from paper_2112_07075_b300.learned import record_examples, train
+    from paper_2112_07075_b300.lh import Context, MLP, learn_attach, learn_stats
+    n, steps = 3, 8
+    V = inputs.box_vertices(3, n, jitter=0.1, seed=9)
+    X, T, rows = record_examples([V], n, steps)
+    assert rows > 0
+    net = MLP(seed=2, max_rows=4096)
+    train(net, X[:rows], T[:rows], epochs=60, batch=512, lr=2e-3)
+    V2 = inputs.box_vertices(3, n, jitter=0.1, seed=10)
+    states = {}
+    for mode in ("plain", "learned"):
+        ctx = Context(3, n, V2, 3, 6, precision="fp32_ir")
+        if mode == "learned":
+            learn_attach(ctx, net, 2)
+        x, v, e = ctx.init_state()
+        info = ctx.new_step_info(0.0, 1.0)
+        for _ in range(steps):
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+        torch.cuda.synchronize()
+        assert ctx.read_step_info(info).status == 0
+        if mode == "learned":
+            st = learn_stats(ctx)
+            assert st["predictions"] == 2 * steps - 3 and st["solves"] == 2 * steps
+        states[mode] = [t.cpu().numpy() for t in (x, v, e)]
+    for a, b in zip(states["learned"], states["plain"]):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+    hy = Hydro(Params(dim=3, n=n, order=3, q1=6, vertices=V2))
+    xo, vo, eo = hy.initial_state("taylor_green")
+    t = 0.0
+    for _ in range(steps):
+        xo, vo, eo, oi = hy.rk2avg_step(xo, vo, eo, dt=None, t=t, t_end=1.0)
+        t += oi.dt
+    for a, b in zip(states["learned"], (xo, vo, eo)):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+    net.close()
