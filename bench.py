@@ -274,9 +274,11 @@ def run_ours(args):
 
     forms = None
     batching = None
+    learned = None
     if not args.no_forms and world == 1:
         forms = forms_report(flush)
         batching = batching_report(flush)
+        learned = learned_report(flush)
     clk.__exit__()
     clocks = clk.summary()
     clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
@@ -296,7 +298,7 @@ def run_ours(args):
             "gpu_launches": 13 * K,
             "clocks": clocks,
             "kernels": kernels,
-            "forms": {"precision": forms, "batching": batching},
+            "forms": {"precision": forms, "batching": batching, "learned": learned},
             "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
             "device_status": status, "wall_s_timed": wall,
         }
@@ -438,6 +440,95 @@ def batching_report(flush, steps=5, warmup=2, seed=4):
     for c in ctxs:
         c.close()
     return rep
+
+
+def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, train_steps=30, epochs=4):
+    """3D Taylor-Green Q3/Q2, q1 = 6, jitter +-0.1h. Train the per-element MLP on
+    examples recorded from `train_seeds` seeded meshes of train_n^3 elements (fixed
+    dt = the CFL step of the eval_n^3 mesh), then step two held-out seeds at
+    eval_n^3 three ways: FP64 with the previous-solve guess, FP32-IR with it, and
+    FP32-IR with the learned guess (fallback to the previous solve by residual)."""
+    import torch
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.learned import record_examples, train
+    from paper_2112_07075_b300.lh import MLP, Context, learn_attach, learn_stats
+    t0 = time.perf_counter()
+    Ve = [inputs.box_vertices(3, eval_n, jitter=0.1, seed=s) for s in (9, 10)]
+    ctx = Context(3, eval_n, Ve[0], 3, 6)
+    x, v, e = ctx.init_state()
+    est = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.update_qdata(x, v, e, est)
+    dt = float(est.item())
+    ctx.close()
+    del x, v, e
+    # training data at train_n^3 with the eval mesh's CFL step
+    import numpy as _np
+    Vt = [inputs.box_vertices(3, train_n, jitter=0.1, seed=s) for s in range(1, train_seeds + 1)]
+    ne = train_n ** 3
+    cap = train_seeds * ne * 2 * train_steps
+    X = torch.zeros((cap, 586), dtype=torch.float32, device="cuda")
+    T = torch.zeros((cap, 192), dtype=torch.float32, device="cuda")
+    rows = 0
+    from paper_2112_07075_b300.lh import learn_attach as _att
+    for V in Vt:
+        c = Context(3, train_n, V, 3, 6)
+        _att(c, None, 1, X[rows:], T[rows:])
+        xs, vs, es = c.init_state()
+        info = c.new_step_info()
+        for _ in range(train_steps):
+            c.rk2avg_step(xs, vs, es, dt, info)
+        torch.cuda.synchronize()
+        rows += learn_stats(c)["rows"]
+        c.close()
+    gen_s = time.perf_counter() - t0
+    net = MLP(seed=7, max_rows=max(8192, eval_n ** 3))
+    t1 = time.perf_counter()
+    hist = train(net, X[:rows], T[:rows], epochs=epochs, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    del X, T
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    out = {"dt": dt, "train_rows": rows, "data_gen_s": gen_s, "train_s": train_s, "train_loss": hist,
+           "config": f"eval {eval_n}^3 Q3 seeds 9,10 x {eval_steps} steps; train {train_seeds} seeds x "
+                     f"{train_steps} steps at {train_n}^3 (reduced from 2000 steps per seed)"}
+    finals = {}
+    for mode in ("fp64", "fp32_ir", "fp32_ir+learned"):
+        ms, its, used, preds = [], [], 0, 0
+        for si, V in enumerate(Ve):
+            c = Context(3, eval_n, V, 3, 6, precision="fp64" if mode == "fp64" else "fp32_ir")
+            if mode.endswith("learned"):
+                learn_attach(c, net, 2)
+            xs, vs, es = c.init_state()
+            info = c.new_step_info()
+            for k in range(eval_steps):
+                flush.fill_(7.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                c.rk2avg_step(xs, vs, es, dt, info)
+                b.record(stream)
+                b.synchronize()
+                if k >= 2:   # the learned guess needs three earlier solves
+                    ms.append(a.elapsed_time(b))
+                    its.append(sum(c.read_step_info(info).cg_iters))
+            if mode.endswith("learned"):
+                st = learn_stats(c)
+                used += st["used"]
+                preds += st["predictions"]
+            if si == 0:
+                finals[mode] = [t.cpu().numpy() for t in (xs, vs, es)]
+            c.close()
+        out[mode] = {"ms_per_step": statistics.mean(ms), "cg_iters_per_step": statistics.mean(its)}
+        if mode.endswith("learned"):
+            out[mode]["learned_guess_used"] = used
+            out[mode]["predictions"] = preds
+    base = finals["fp64"]
+    for mode in ("fp32_ir", "fp32_ir+learned"):
+        out[mode]["max_rel_field_diff_vs_fp64_gpu"] = max(
+            float(_np.linalg.norm(a - b) / _np.linalg.norm(b)) for a, b in zip(finals[mode], base))
+        out[mode]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out[mode]["ms_per_step"]
+    net.close()
+    return out
 
 
 # ---------------------------------------------------------------------------

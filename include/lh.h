@@ -257,10 +257,11 @@ void lh_batch_destroy(lh_batch *b);
  * velocity mass solves of lh_rk2avg_step. Network: 586 -> 128 -> 128 -> 192,
  * GELU (erf) after both hidden layers, BF16 weights and activations on the
  * tensor cores with FP32 accumulation, FP32 master weights, Adam (0.9, 0.999,
- * 1e-8), mean-squared-error loss. Inputs per element (3D Q3): the three most
- * recent mass-solve solutions at its 64 nodes divided by the RMS s of the latest
- * one (576 values, most recent first), its Jacobian at the centroid divided by
- * h0*p (9) and det J / (h0*p)^3 (1). Output: (a_new - a_latest) / s at its nodes.
+ * 1e-8), mean-squared-error loss. Inputs per element (3D Q3), from the three most
+ * recent mass-solve solutions a_1, a_2, a_3 at its 64 nodes (3 x 192 values):
+ * a_1 / s, (a_1 - a_2) / s_d and (a_2 - a_3) / s_d with s, s_d the RMS of a_1 and
+ * of a_1 - a_2 over the free DOFs; then its Jacobian at the centroid divided by
+ * h0*p (9) and det J / (h0*p)^3 (1). Output: (a_new - a_1) / s_d at its nodes.
  * Parameters are one flat FP32 vector: W1 [128][592] (input padded to 592;
  * columns 586..591 stay zero), b1[128], W2 [128][128], b2[128], W3 [192][128], b3[192].
  * ------------------------------------------------------------------------- */

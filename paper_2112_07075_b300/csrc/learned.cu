@@ -3,13 +3,15 @@
 // element's Jacobian at its centroid. Supported for 3D Q3 (64 nodes x 3
 // components = 192 outputs per element) with q1 = 6.
 //
-// Per solve of lh_rk2avg_step, with s = RMS of the latest solution a_1 over the
-// free DOFs:
-//   features  X_e = [a_1, a_2, a_3 at the element's nodes] / s (576 values, most
-//             recent first) ++ [J(centroid) / (h0 p), det J / (h0 p)^3] (10 values)
-//   target    T_e = (a_new - a_1) / s at the element's nodes (recording mode)
-//   guess     g = a_1 + s * (average over the elements sharing each node of the
+// Per solve of lh_rk2avg_step, with a_1, a_2, a_3 the three most recent solutions,
+// s = RMS of a_1 and s_d = RMS of a_1 - a_2 over the free DOFs:
+//   features  X_e = [a_1 / s, (a_1 - a_2) / s_d, (a_2 - a_3) / s_d at the element's
+//             nodes] (576 values) ++ [J(centroid) / (h0 p), det J / (h0 p)^3] (10)
+//   target    T_e = (a_new - a_1) / s_d at the element's nodes (recording mode)
+//   guess     g = a_1 + s_d * (average over the elements sharing each node of the
 //             MLP output), zero on constrained DOFs (prediction mode)
+// Successive solutions differ by a small fraction of their size, so the history
+// enters as normalised differences: raw solutions rounded to BF16 would lose it.
 // In prediction mode the residuals ||b - M g|| and ||b - M a_1|| are compared
 // (FP32 mass action, FP64 sums) and the smaller one's vector starts CG; the CG
 // tolerance is unchanged, so the guess only changes the iteration count.
@@ -37,40 +39,52 @@ constexpr int kBlocks = 592;
 
 struct Cent { double v[4], d[4]; };   // 1D basis values / derivatives at the centre 0.5
 
-__global__ void k_sumsq(size_t nv, const double *__restrict__ a, const double *__restrict__ idg,
-                        double *__restrict__ part) {
-  double acc = 0.0, cnt = 0.0;
+__global__ void k_sumsq(size_t nv, const double *__restrict__ a1, const double *__restrict__ a2,
+                        const double *__restrict__ idg, double *__restrict__ part) {
+  double v[3] = {0.0, 0.0, 0.0};
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (size_t)gridDim.x * blockDim.x)
-    if (idg[k] != 0.0) { acc = fma(a[k], a[k], acc); cnt += 1.0; }
-  double v[2] = {acc, cnt};
-  __shared__ double red[64];
-  block_sum<2>(v, red);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = v[0]; part[2 * blockIdx.x + 1] = v[1]; }
+    if (idg[k] != 0.0) {
+      const double d = a1[k] - a2[k];
+      v[0] = fma(a1[k], a1[k], v[0]);
+      v[1] = fma(d, d, v[1]);
+      v[2] += 1.0;
+    }
+  __shared__ double red[96];
+  block_sum<3>(v, red);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[3 * blockIdx.x + q] = v[q];
 }
+// s[0] = RMS of a_1, s[1] = RMS of a_1 - a_2 (1 where zero)
 __global__ void k_scale_final(int nb, const double *__restrict__ part, double *__restrict__ s) {
   if (threadIdx.x < 32) {
-    double a = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < nb; i += 32) { a += part[2 * i]; c += part[2 * i + 1]; }
+    double a = 0.0, d = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) { a += part[3 * i]; d += part[3 * i + 1]; c += part[3 * i + 2]; }
     a = warp_sum(a);
+    d = warp_sum(d);
     c = warp_sum(c);
     if (threadIdx.x == 0) {
-      const double rms = c > 0.0 ? sqrt(a / c) : 0.0;
-      *s = rms > 0.0 ? rms : 1.0;
+      const double ra = c > 0.0 ? sqrt(a / c) : 0.0, rd = c > 0.0 ? sqrt(d / c) : 0.0;
+      s[0] = ra > 0.0 ? ra : 1.0;
+      s[1] = rd > 0.0 ? rd : 1.0;
     }
   }
 }
 
-// History features: X[row0 + e][k*192 + c*64 + i] = hist_k[c][node(e,i)] / s.
+// History features: X[e][c*64 + i] = a_1 / s, X[e][192 + c*64 + i] = (a_1 - a_2) / s_d,
+// X[e][384 + c*64 + i] = (a_2 - a_3) / s_d at node(e, i), component c.
 __global__ void k_hist_features(MeshDesc m, const double *__restrict__ h0, const double *__restrict__ h1,
                                 const double *__restrict__ h2, const double *__restrict__ s, float *__restrict__ X) {
   const size_t total = (size_t)m.ne * 576;
-  const double is = 1.0 / *s;
+  const double is = 1.0 / s[0], isd = 1.0 / s[1];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int e = (int)(t / 576), f = (int)(t % 576);
     const int k = f / 192, c = (f / 64) % 3, i = f % 64;
-    const double *h = k == 0 ? h0 : (k == 1 ? h1 : h2);
-    const int g = h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
-    X[(size_t)e * kIn + f] = (float)(h[(size_t)c * m.nh1 + g] * is);
+    const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
+    double val;
+    if (k == 0) val = h0[gi] * is;
+    else if (k == 1) val = (h0[gi] - h1[gi]) * isd;
+    else val = (h1[gi] - h2[gi]) * isd;
+    X[(size_t)e * kIn + f] = (float)val;
   }
 }
 
@@ -101,11 +115,11 @@ __global__ void k_jac_features(MeshDesc m, const double *__restrict__ x, Cent cb
   }
 }
 
-// Targets: T[row0 + e][c*64 + i] = (a_new - a_1)[c][node(e,i)] / s.
+// Targets: T[e][c*64 + i] = (a_new - a_1)[c][node(e,i)] / s_d.
 __global__ void k_targets(MeshDesc m, const double *__restrict__ anew, const double *__restrict__ a1,
                           const double *__restrict__ s, float *__restrict__ T) {
   const size_t total = (size_t)m.ne * kOut;
-  const double is = 1.0 / *s;
+  const double is = 1.0 / s[1];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int e = (int)(t / kOut), f = (int)(t % kOut);
     const int c = f / 64, i = f % 64;
@@ -114,10 +128,10 @@ __global__ void k_targets(MeshDesc m, const double *__restrict__ anew, const dou
   }
 }
 
-// Guess at nodes: g = a_1 + s * mean over element copies of the MLP output; 0 on constrained DOFs.
+// Guess at nodes: g = a_1 + s_d * mean over element copies of the MLP output; 0 on constrained DOFs.
 __global__ void k_assemble(MeshDesc m, const float *__restrict__ Y, const double *__restrict__ a1,
                            const double *__restrict__ s, const double *__restrict__ idg, double *__restrict__ g) {
-  const double sc = *s;
+  const double sc = s[1];
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < m.nh1; n += gridDim.x * blockDim.x) {
     int off[8];
     const int cnt = node_copies<3, D>(m, n, 3, off);
@@ -246,7 +260,7 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
   const MeshDesc &m = c->mesh;
   const size_t nv = c->nv;
   const double *a1 = hist_at(L, 0);
-  k_sumsq<<<kBlocks, 256, 0, s>>>(nv, a1, c->invdiag, L->part);
+  k_sumsq<<<kBlocks, 256, 0, s>>>(nv, a1, hist_at(L, 1), c->invdiag, L->part);
   k_scale_final<<<1, 32, 0, s>>>(kBlocks, L->part, L->scale);
   float *X = L->X;
   L->pending = false;
@@ -359,8 +373,8 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   char *misc = take(bytes_list[6]);
   L->part = (double *)misc;
   L->scale = (double *)(misc + 4 * 1184 * 8);
-  L->ratio = L->scale + 1;
-  L->flag = (int *)(L->scale + 2);
+  L->ratio = L->scale + 2;
+  L->flag = (int *)(L->scale + 3);
   L->used = L->flag + 1;
   lh::h1_basis_at(3, 0.5, L->cent.v, L->cent.d);
   L->hs = c->h0 * c->p;

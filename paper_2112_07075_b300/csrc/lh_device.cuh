@@ -70,6 +70,58 @@ __device__ __forceinline__ void contract2(const double *__restrict__ in1, const 
 }
 
 // ---------------------------------------------------------------------------
+// Pencil form of `contract`: one thread owns a whole pencil (a, b): it loads
+// in[a][0..K-1][b] into registers once and writes out[a][0..O-1][b]. Matrix
+// entries are read as warp-uniform shared-memory broadcasts. Fewer address and
+// shared-memory instructions per multiply-add than one-output-per-step loops,
+// which matters where the arithmetic itself is cheap (FP32); the O x K matrix
+// is kept in registers.
+// ---------------------------------------------------------------------------
+template <int A, int K, int O, int BS, typename T>
+__device__ __forceinline__ void contract_p(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ Ms) {
+  constexpr int NP = A * BS;
+  T M[O * K];   // the 1D matrix, held in registers for the whole stage
+#pragma unroll
+  for (int j = 0; j < O * K; ++j) M[j] = Ms[j];
+  for (int idx = threadIdx.x; idx < NP; idx += blockDim.x) {
+    const int b = idx % BS;
+    const int a = idx / BS;
+    const T *ip = in + a * K * BS + b;
+    T v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = ip[k * BS];
+    T *op = out + a * O * BS + b;
+#pragma unroll
+    for (int o = 0; o < O; ++o) {
+      T s = M[o * K] * v[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) s = fma(M[o * K + k], v[k], s);
+      op[o * BS] = s;
+    }
+  }
+}
+
+// Pencil-form tensor-product interpolation (same result layout as interp).
+template <int DIM, int NI, int NO, int C, typename T>
+__device__ __forceinline__ void interp_p(const T *__restrict__ in, T *__restrict__ out, T *__restrict__ S,
+                                         const T *__restrict__ M) {
+  if constexpr (DIM == 2) {
+    contract_p<C * NI, NI, NO, 1>(in, S, M);
+    __syncthreads();
+    contract_p<C, NI, NO, NO>(S, out, M);
+    __syncthreads();
+  } else {
+    T *t2 = S + C * NI * NI * NO;
+    contract_p<C * NI * NI, NI, NO, 1>(in, S, M);
+    __syncthreads();
+    contract_p<C * NI, NI, NO, NO>(S, t2, M);
+    __syncthreads();
+    contract_p<C, NI, NO, NO * NO>(t2, out, M);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Scratch sizes (doubles) of the helpers below, for C tensors.
 // ---------------------------------------------------------------------------
 template <int DIM, int NI, int NO>

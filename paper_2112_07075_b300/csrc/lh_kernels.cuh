@@ -692,6 +692,73 @@ struct Family {
     }
   }
 
+  // FP32 sweeps of the precision form use their own, larger element batches
+  // (FP32 arithmetic is cheap, so batch latency dominates): as many elements as
+  // fit in ~96 KB of shared memory, at most 64.
+  static constexpr int PER_ELEM_F = 2 * DIM * ND + DIM * NQ +
+                                    (interp_scratch<DIM, D, Q>(DIM) > interp_scratch<DIM, Q, D>(DIM)
+                                         ? interp_scratch<DIM, D, Q>(DIM) : interp_scratch<DIM, Q, D>(DIM));
+#ifndef LH_NBF_FLOATS
+#define LH_NBF_FLOATS 24000
+#endif
+  static constexpr int NBF_RAW = LH_NBF_FLOATS / PER_ELEM_F;
+  static constexpr int NBF = NBF_RAW < 1 ? 1 : (NBF_RAW > 64 ? 64 : NBF_RAW);
+  static constexpr int CXF = NBF * DIM;
+  static constexpr int MF_S = max3(interp_scratch<DIM, D, Q>(CXF), interp_scratch<DIM, Q, D>(CXF), 0);
+  static constexpr int NB_EB = NBF > NBC ? NBF : NBC;   // size of the per-batch base-node table
+
+  template <int MODE>
+  static __device__ __forceinline__ void sweep_matvec_f(const MeshDesc &m, int *eb, const float *tb,
+                                                        const float *tbt, float *u, float *S, float *uq, float *y,
+                                                        const float *mq, const float *idv, const float *x,
+                                                        const float *r, const float *q, const float *p, float alpha,
+                                                        float beta, float *evec) {
+    const int nbatch = (m.ne + NBF - 1) / NBF;
+    constexpr int MQT = (CXF * NQ + TC - 1) / TC;   // mass-data values per thread (blockDim == TC)
+    for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+      const int e0 = bt * NBF, nb = min(NBF, m.ne - e0);
+      // issue this batch's mass-data loads first: they are needed only after the
+      // first contraction stages, so their latency overlaps the gather and stages
+      // (only while the prefetch array is small: more registers would cost occupancy)
+      constexpr bool kPrefetch = MQT <= 16;
+      float mqr[kPrefetch ? MQT : 1];
+      if constexpr (kPrefetch) {
+#pragma unroll
+        for (int j = 0; j < MQT; ++j) {
+          const int k = threadIdx.x + j * TC;
+          const int qq = k % NQ, b = (k / NQ) / DIM;
+          mqr[j] = (k < CXF * NQ && b < nb) ? mq[(size_t)(e0 + b) * NQ + qq] : 0.0f;
+        }
+      }
+      if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, e0 + threadIdx.x);
+      __syncthreads();
+      for (int k = threadIdx.x; k < CXF * ND; k += blockDim.x) {
+        const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+        float val = 0.0f;
+        if (b < nb) val = dir_value<MODE, float>(c * m.nh1 + eb[b] + h1_local<DIM, D>(m, i), idv, x, r, q, p, alpha, beta);
+        u[k] = val;
+      }
+      __syncthreads();
+      interp_p<DIM, D, Q, CXF>(u, uq, S, tb);
+      if constexpr (kPrefetch) {
+#pragma unroll
+        for (int j = 0; j < MQT; ++j) {
+          const int k = threadIdx.x + j * TC;
+          if (k < CXF * NQ) uq[k] *= mqr[j];
+        }
+      } else {
+        for (int k = threadIdx.x; k < CXF * NQ; k += blockDim.x) {
+          const int qq = k % NQ, b = (k / NQ) / DIM;
+          uq[k] *= b < nb ? mq[(size_t)(e0 + b) * NQ + qq] : 0.0f;
+        }
+      }
+      __syncthreads();
+      interp_p<DIM, Q, D, CXF>(uq, y, S, tbt);
+      for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) evec[(size_t)e0 * DIM * ND + k] = y[k];
+      __syncthreads();
+    }
+  }
+
   // Node sweep that closes iteration k and opens k+1 (MODE 2), or starts the
   // solve (MODE 1: p = invdiag r): r' = r - alpha q, x' = x + alpha p,
   // p' = invdiag r' + beta p, q' = gathered E-vector; accumulates
@@ -891,7 +958,7 @@ struct Family {
   // two-barrier Jacobi PCG on M d = r from d = 0 to a relative residual
   // inner_tol, with FP32 tables, mass data, vectors, element vectors, partial
   // sums and scalars.
-  static constexpr int IR_F = 2 * Q * D + CXC * ND + MC_S + CXC * NQ + CXC * ND;   // floats
+  static constexpr int IR_F = 2 * Q * D + CXF * ND + MF_S + CXF * NQ + CXF * ND;   // floats
   static constexpr int IR_D = CXC * ND + MC_S + CXC * NQ + CXC * ND;               // doubles
   static constexpr int IR_R = (IR_F + 1) / 2 > IR_D ? (IR_F + 1) / 2 : IR_D;
   static constexpr size_t cg_ir_smem() { return sizeof(double) * (TAB + IR_R + RED); }
@@ -899,12 +966,12 @@ struct Family {
     extern __shared__ double sm[];
     double *st = sm, *R = st + TAB, *red = R + IR_R;
     double *u = R, *S = u + CXC * ND, *uq = S + MC_S, *y = uq + CXC * NQ;                 // FP64 view
-    float *tb = (float *)R, *tbt = tb + Q * D, *uf = tbt + Q * D, *Sf = uf + CXC * ND;    // FP32 view
-    float *uqf = Sf + MC_S, *yf = uqf + CXC * NQ;
+    float *tb = (float *)R, *tbt = tb + Q * D, *uf = tbt + Q * D, *Sf = uf + CXF * ND;    // FP32 view
+    float *uqf = Sf + MF_S, *yf = uqf + CXF * NQ;
     float *redf = (float *)red;
     __shared__ double s_sc[4];
     __shared__ float s_f[4];
-    __shared__ int s_eb[NBC];
+    __shared__ int s_eb[NB_EB];
     const MeshDesc &m = a.mesh;
     const int G = gridDim.x;
     const int nh1 = m.nh1;
@@ -1027,15 +1094,20 @@ struct Family {
         tb[k] = (float)(k < Q * D ? st[oB + k] : st[oBt + k - Q * D]);
       __syncthreads();
       float rr = s_f[0], rz = s_f[1], rz_old = rz;
-      const float target = (float)(a.inner_tol * a.inner_tol) * rr;
+      // relative reduction of this inner solve: inner_tol, or less when a smaller
+      // step reaches the FP64 tolerance (0.1 safety factor): a good initial guess
+      // then saves inner iterations instead of only whole refinement steps
+      const double need = 0.1 * a.tol * sqrt(bb / fmax(rr64, 1e-300));
+      const double red_rel = fmax(a.inner_tol, fmin(need, 1.0));
+      const float target = (float)(red_rel * red_rel) * rr;
       int it = 0;
       for (;;) {
         if (rr <= target || it >= a.max_inner) break;
         const float beta = it == 0 ? 0.0f : rz / rz_old;
         rz_old = rz;
         // E: FP32 E-vector of M p_new, p_new = invdiag r + beta p
-        sweep_matvec<3, float>(m, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32, a.p32,
-                               0.0f, beta, a.evec32);
+        sweep_matvec_f<3>(m, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32, a.p32,
+                          0.0f, beta, a.evec32);
         if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
         {  // q = M p_new gathered, p = p_new, p.q
           float acc[5] = {0, 0, 0, 0, 0};
