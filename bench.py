@@ -442,7 +442,7 @@ def batching_report(flush, steps=5, warmup=2, seed=4):
     return rep
 
 
-def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, train_steps=30, epochs=4):
+def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, train_steps=30, epochs=8):
     """3D Taylor-Green Q3/Q2, q1 = 6, jitter +-0.1h. Train the per-element MLP on
     examples recorded from `train_seeds` seeded meshes of train_n^3 elements (fixed
     dt = the CFL step of the eval_n^3 mesh), then step two held-out seeds at
@@ -493,10 +493,10 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
            "config": f"eval {eval_n}^3 Q3 seeds 9,10 x {eval_steps} steps; train {train_seeds} seeds x "
                      f"{train_steps} steps at {train_n}^3 (reduced from 2000 steps per seed)"}
     finals = {}
-    for mode in ("fp64", "fp32_ir", "fp32_ir+learned"):
-        ms, its, used, preds = [], [], 0, 0
+    for mode in ("fp64", "fp64+learned", "fp32_ir", "fp32_ir+learned"):
+        ms, its, used, preds, ratios = [], [], 0, 0, []
         for si, V in enumerate(Ve):
-            c = Context(3, eval_n, V, 3, 6, precision="fp64" if mode == "fp64" else "fp32_ir")
+            c = Context(3, eval_n, V, 3, 6, precision="fp64" if mode.startswith("fp64") else "fp32_ir")
             if mode.endswith("learned"):
                 learn_attach(c, net, 2)
             xs, vs, es = c.init_state()
@@ -515,6 +515,7 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
                 st = learn_stats(c)
                 used += st["used"]
                 preds += st["predictions"]
+                ratios.append(st["mean_residual_ratio"])
             if si == 0:
                 finals[mode] = [t.cpu().numpy() for t in (xs, vs, es)]
             c.close()
@@ -522,8 +523,9 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
         if mode.endswith("learned"):
             out[mode]["learned_guess_used"] = used
             out[mode]["predictions"] = preds
+            out[mode]["mean_initial_residual_ratio_learned_vs_previous"] = statistics.mean(ratios)
     base = finals["fp64"]
-    for mode in ("fp32_ir", "fp32_ir+learned"):
+    for mode in ("fp64+learned", "fp32_ir", "fp32_ir+learned"):
         out[mode]["max_rel_field_diff_vs_fp64_gpu"] = max(
             float(_np.linalg.norm(a - b) / _np.linalg.norm(b)) for a, b in zip(finals[mode], base))
         out[mode]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out[mode]["ms_per_step"]

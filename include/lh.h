@@ -291,16 +291,19 @@ const char *lh_mlp_last_error(const lh_mlp *m);
  * training example per element at every mass solve of lh_rk2avg_step that has
  * three earlier solutions (features into X_buf[row][586], targets into
  * T_buf[row][192], DEVICE, until capacity_rows rows are filled). mode 2: predict
- * the initial guess with `mlp` (context precision must be LH_PRECISION_FP32_IR):
- * the guess g and the previous solution are compared by ||b - M .||_2 (FP32
- * mass action, FP64 sums) and the smaller starts CG; CG still runs to its
- * tolerance. mode 0: detach. Allocates the form's device buffers (a set-up
- * call); synchronous. */
+ * the initial guess with `mlp`: the guess g and the previous solution are
+ * compared by the Jacobi-preconditioned residual norm (r, D^-1 r), r = b - M .
+ * (FP32 mass action, FP64 sums), and the smaller starts CG; CG still runs to its
+ * tolerance (either precision). mode 0: detach.
+ * Allocates the form's device buffers (a set-up call); synchronous. */
 lh_status lh_learn_attach(lh_ctx *ctx, lh_mlp *mlp, int mode, float *X_buf, float *T_buf, int capacity_rows);
 /* HOST counters of the attached learned form: rows recorded, mass solves seen,
- * predictions made, predictions that won the residual comparison (the last
- * one reads device memory; synchronous). Any pointer may be NULL. */
-lh_status lh_learn_stats(const lh_ctx *ctx, int *rows_recorded, int *solves, int *predictions, int *learned_used);
+ * predictions made, predictions that won the residual comparison, and the mean
+ * over predictions of the ratio of the two compared norms, learned over previous
+ * (square root of (r, D^-1 r) ratios; the last two read
+ * device memory; synchronous). Any pointer may be NULL. */
+lh_status lh_learn_stats(const lh_ctx *ctx, int *rows_recorded, int *solves, int *predictions, int *learned_used,
+                         double *mean_ratio);
 
 /* Mass product without any device allocation (the paper has no counterpart; this
  * is a convenience of this library). Computes the same y = M_v x as lh_mass_mult,

@@ -12,9 +12,10 @@
 //             MLP output), zero on constrained DOFs (prediction mode)
 // Successive solutions differ by a small fraction of their size, so the history
 // enters as normalised differences: raw solutions rounded to BF16 would lose it.
-// In prediction mode the residuals ||b - M g|| and ||b - M a_1|| are compared
-// (FP32 mass action, FP64 sums) and the smaller one's vector starts CG; the CG
-// tolerance is unchanged, so the guess only changes the iteration count.
+// In prediction mode the Jacobi-preconditioned residual norms (r, D^-1 r) of g and
+// a_1 are compared (FP32 mass action, FP64 sums) and the smaller one's vector
+// starts CG; the CG tolerance is unchanged, so the guess only changes the
+// iteration count.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -180,7 +181,8 @@ __global__ void __launch_bounds__(F::THREADS) k_resid_elem(MeshDesc m, const dou
   }
 }
 
-// Residual norms of both candidates: per-block partials (FP64 sums of FP32 residuals).
+// Preconditioned residual norms (r, D^-1 r) of both candidates -- the quantity
+// Jacobi-PCG itself reduces -- as per-block partials (FP64 sums of FP32 residuals).
 __global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const double *__restrict__ idg,
                               const float *__restrict__ evA, const float *__restrict__ evB, double *__restrict__ part) {
   double acc[2] = {0.0, 0.0};
@@ -193,8 +195,8 @@ __global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const do
       float ma = 0.0f, mb = 0.0f;
       for (int j = 0; j < cnt; ++j) { ma += evA[off[j] + c * ND]; mb += evB[off[j] + c * ND]; }
       const double ra = b[k] - (double)ma, rb = b[k] - (double)mb;
-      acc[0] = fma(ra, ra, acc[0]);
-      acc[1] = fma(rb, rb, acc[1]);
+      acc[0] = fma(ra * idg[k], ra, acc[0]);   // Jacobi-preconditioned residual norms (r, D^-1 r)
+      acc[1] = fma(rb * idg[k], rb, acc[1]);
     }
   }
   __shared__ double red[64];
@@ -202,9 +204,9 @@ __global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const do
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = acc[0]; part[2 * blockIdx.x + 1] = acc[1]; }
 }
 
-// Decide (one warp) and count: flag = ||b - M g|| < ||b - M a_1||.
+// Decide (one warp) and count: flag = (r_g, D^-1 r_g) < (r_1, D^-1 r_1).
 __global__ void k_decide(int nb, const double *__restrict__ part, int *__restrict__ flag, int *__restrict__ used,
-                         double *__restrict__ ratio) {
+                         double *__restrict__ ratio_sum) {
   if (threadIdx.x < 32) {
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) { a += part[2 * i]; b += part[2 * i + 1]; }
@@ -214,9 +216,14 @@ __global__ void k_decide(int nb, const double *__restrict__ part, int *__restric
       const int f = a < b ? 1 : 0;
       *flag = f;
       *used += f;
-      *ratio = b > 0.0 ? sqrt(a / b) : 1.0;
+      *ratio_sum += b > 0.0 ? sqrt(a / b) : 1.0;
     }
   }
+}
+
+__global__ void k_to_f32(size_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    b[k] = (float)a[k];
 }
 
 __global__ void k_apply(size_t nv, const int *__restrict__ flag, const double *__restrict__ g, double *__restrict__ a) {
@@ -236,6 +243,7 @@ struct lh_learn {
   double *hist[3] = {nullptr, nullptr, nullptr};
   int count = 0, head = 0;   // solutions stored, next ring slot
   float *X = nullptr, *Y = nullptr, *evB = nullptr, *evA32 = nullptr;
+  float *mq32 = nullptr;     // FP32 mass data for the residual check (own copy for FP64 contexts)
   double *guess = nullptr, *scale = nullptr, *part = nullptr, *ratio = nullptr;
   int *flag = nullptr, *used = nullptr;
   float *dX = nullptr, *dT = nullptr;
@@ -275,7 +283,7 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
     if (lh_status st = lh_mlp_forward(L->mlp, X, m.ne, L->Y, (lh_stream_t)s)) return st;
     k_assemble<<<2 * kBlocks, 256, 0, s>>>(m, L->Y, a1, L->scale, c->invdiag, L->guess);
     k_resid_elem<<<c->grid_elem, F::THREADS, L->smem_resid, s>>>(
-        m, c->tab, c->mq32, L->guess, a1, c->invdiag, L->evA32, L->evB);
+        m, c->tab, L->mq32, L->guess, a1, c->invdiag, L->evA32, L->evB);
     k_resid_nodes<<<kBlocks, 256, 0, s>>>(m, c->rhs, c->invdiag, L->evA32, L->evB, L->part);
     k_decide<<<1, 32, 0, s>>>(kBlocks, L->part, L->flag, L->used, L->ratio);
     k_apply<<<kBlocks, 256, 0, s>>>(nv, L->flag, L->guess, c->a_prev);
@@ -337,8 +345,8 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
     c->err = "recording needs example buffers";
     return LH_ERR_ARG;
   }
-  if (mode == 2 && (!mlp || c->prm.precision != LH_PRECISION_FP32_IR)) {
-    c->err = "prediction needs an MLP and a context with LH_PRECISION_FP32_IR";
+  if (mode == 2 && !mlp) {
+    c->err = "prediction needs an MLP";
     return LH_ERR_ARG;
   }
   if (mode != 1 && mode != 2) { c->err = "mode must be 0, 1 or 2"; return LH_ERR_ARG; }
@@ -351,8 +359,10 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   L->dT = T_buf;
   L->capacity = capacity_rows;
   const size_t nv = c->nv, ne = c->mesh.ne;
+  const bool own_mq32 = c->mq32 == nullptr;
+  const size_t nq = ne * (size_t)c->nq;
   const size_t bytes_list[] = {3 * nv * 8, ne * lh::mlp::kIn * 4, ne * lh::mlp::kOut * 4, ne * 3 * 64 * 4,
-                               ne * 3 * 64 * 4, nv * 8, 4 * 1184 * 8 + 1024};
+                               ne * 3 * 64 * 4, nv * 8, 4 * 1184 * 8 + 1024, own_mq32 ? nq * 4 : 0};
   size_t bytes = 0;
   for (size_t b : bytes_list) bytes += (b + 255) / 256 * 256;
   if (cudaMalloc(&L->arena, bytes) != cudaSuccess) {
@@ -371,6 +381,7 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   L->evB = (float *)take(bytes_list[4]);
   L->guess = (double *)take(bytes_list[5]);
   char *misc = take(bytes_list[6]);
+  L->mq32 = own_mq32 ? (float *)take(bytes_list[7]) : c->mq32;
   L->part = (double *)misc;
   L->scale = (double *)(misc + 4 * 1184 * 8);
   L->ratio = L->scale + 2;
@@ -382,11 +393,13 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
                                        lh::learn::F::CX * lh::learn::F::NQ + lh::learn::F::CX * 64) + 16;
   cudaFuncSetAttribute((const void *)lh::learn::k_resid_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   L->smem_resid = smem;
+  if (own_mq32) lh::learn::k_to_f32<<<1024, 256>>>(nq, c->mq, L->mq32);
   c->learn = L;
   return cudaDeviceSynchronize() == cudaSuccess ? LH_OK : LH_ERR_CUDA;
 }
 
-lh_status lh_learn_stats(const lh_ctx *c, int *rows_recorded, int *solves, int *predictions, int *learned_used) {
+lh_status lh_learn_stats(const lh_ctx *c, int *rows_recorded, int *solves, int *predictions, int *learned_used,
+                         double *mean_ratio) {
   if (!c || !c->learn) return LH_ERR_ARG;
   const lh_learn *L = c->learn;
   if (rows_recorded) *rows_recorded = L->rows;
@@ -394,6 +407,11 @@ lh_status lh_learn_stats(const lh_ctx *c, int *rows_recorded, int *solves, int *
   if (predictions) *predictions = L->predicted;
   if (learned_used) {
     if (cudaMemcpy(learned_used, L->used, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LH_ERR_CUDA;
+  }
+  if (mean_ratio) {
+    double sum = 0.0;
+    if (cudaMemcpy(&sum, L->ratio, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return LH_ERR_CUDA;
+    *mean_ratio = L->predicted > 0 ? sum / L->predicted : 0.0;
   }
   return LH_OK;
 }

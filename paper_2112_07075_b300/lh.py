@@ -100,7 +100,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mlp_train_step": (I, [P, VP, VP, I, ctypes.c_float, VP, VP]),
         "lh_mlp_last_error": (ctypes.c_char_p, [P]),
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
-        "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                               ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -378,5 +379,7 @@ def learn_attach(ctx, mlp, mode, X_buf=None, T_buf=None):
 
 def learn_stats(ctx):
     vals = [ctypes.c_int() for _ in range(4)]
-    ctx._check(ctx.lib.lh_learn_stats(ctx.h, *[ctypes.byref(v) for v in vals]))
-    return dict(rows=vals[0].value, solves=vals[1].value, predictions=vals[2].value, used=vals[3].value)
+    ratio = ctypes.c_double()
+    ctx._check(ctx.lib.lh_learn_stats(ctx.h, *[ctypes.byref(v) for v in vals], ctypes.byref(ratio)))
+    return dict(rows=vals[0].value, solves=vals[1].value, predictions=vals[2].value, used=vals[3].value,
+                mean_residual_ratio=ratio.value)
