@@ -49,6 +49,22 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def max_over_ranks(t_local: float, world: int, device: str) -> float:
+    """The slowest rank's timed duration (all ranks receive it)."""
+    if world <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(nv_per_rank: int, steps: int, world: int, t_max: float) -> float:
+    """Whole-job MDOF/s: every rank advanced nv_per_rank DOFs for `steps` steps."""
+    return nv_per_rank * steps * world / t_max / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -191,12 +207,8 @@ def run_ours(args):
     t_local = sum(step_ms) / 1e3
     si = ctx.read_step_info(info)
     status = ctx.sync_status()
-    t_max = t_local
-    if world > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = sz.nv * K * world / t_max / 1e6
+    t_max = max_over_ranks(t_local, world, "cuda")
+    value = job_rate(sz.nv, K, world, t_max)
 
     # ---- per-kernel breakdown at the current state (same stream, CUDA events)
     W = work_model(dim, p, q1, sz.ne, sz.n_h1)

@@ -338,6 +338,13 @@ lh_status lh_learn_stats(const lh_ctx *ctx, int *rows_recorded, int *solves, int
 lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int order, int q1, const double *mq,
                                const double *x, double *y, lh_stream_t stream);
 
+/* Diagnostic (no counterpart in the paper): runs the library's bounded
+ * grid-wide wait with one block that never arrives, so the waiting block gives
+ * up after about one second instead of hanging; writes the device status it
+ * latched (LH_ERR_TIMEOUT when the bound works) to *status_out. Allocates and
+ * frees 256 bytes; synchronous. */
+lh_status lh_selftest_barrier_timeout(int *status_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -630,3 +630,36 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Diagnostic: exercise the bounded grid-barrier timeout without any fault.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_selftest_barrier(GridBarrier *bar, int *status) {
+  if (blockIdx.x == gridDim.x - 1) return;   // this block never arrives
+  grid_sync(bar, gridDim.x, status);          // the others give up after ~1 s
+}
+}  // namespace
+
+extern "C" lh_status lh_selftest_barrier_timeout(int *status_out) {
+  if (!status_out) return LH_ERR_ARG;
+  GridBarrier *bar = nullptr;
+  int *st = nullptr;
+  void *mem = nullptr;
+  if (cudaMalloc(&mem, 256) != cudaSuccess) return LH_ERR_OOM;
+  cudaMemset(mem, 0, 256);
+  bar = (GridBarrier *)mem;
+  st = (int *)((char *)mem + 128);
+  void *args[] = {&bar, &st};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_selftest_barrier, dim3(2), dim3(32), args, 0, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(mem);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("barrier self-test: ") + cudaGetErrorString(e));
+    return LH_ERR_CUDA;
+  }
+  *status_out = h;
+  return LH_OK;
+}

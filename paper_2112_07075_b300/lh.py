@@ -29,7 +29,7 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy",
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_learn_attach",
-            "lh_learn_stats"]
+            "lh_learn_stats", "lh_selftest_barrier_timeout"]
 
 
 class LhParams(ctypes.Structure):
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mlp_train_step": (I, [P, VP, VP, I, ctypes.c_float, VP, VP]),
         "lh_mlp_last_error": (ctypes.c_char_p, [P]),
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
+        "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
     }

@@ -226,3 +226,29 @@ def test_setup_rejects_inverted_mesh_and_unsupported_order():
         _ctx(2, 2, 1, 2, V)
     with pytest.raises(LhError):
         _ctx(2, 2, 2, 7, inputs.box_vertices(2, 2))
+
+
+def test_bounded_grid_wait_times_out_without_fault():
+    """A grid-wide wait whose partner block never arrives gives up (~1 s) and reports LH_ERR_TIMEOUT."""
+    import ctypes
+    from paper_2112_07075_b300 import lh
+    st = ctypes.c_int(-1)
+    assert lh.load_library().lh_selftest_barrier_timeout(ctypes.byref(st)) == lh.LH_OK
+    assert st.value == lh.LH_ERR_TIMEOUT
+
+
+def test_config2_full_size_one_step_matches_oracle():
+    """3D Taylor-Green 24^3, Q2/Q1, 4^3 Gauss points, one CFL (0.5) step from t = 0 -- the benchmarked
+    workload at full size and launch configuration -- against the oracle, 1e-11 per field."""
+    V = inputs.box_vertices(3, 24)
+    hy = _hydro(3, 24, 2, 4, V)
+    ctx = _ctx(3, 24, 2, 4, V)
+    xo, vo, eo = hy.initial_state("taylor_green")
+    xo, vo, eo, oi = hy.rk2avg_step(xo, vo, eo, dt=None, t=0.0, t_end=0.1)
+    xg, vg, eg = ctx.init_state("taylor_green")
+    info = ctx.new_step_info(0.0, 0.1)
+    ctx.rk2avg_step(xg, vg, eg, 0.0, info)
+    si = ctx.read_step_info(info)
+    assert si.status == 0 and abs(si.dt - oi.dt) <= 1e-12 * oi.dt
+    for a, b in ((_np(xg), xo), (_np(vg), vo), (_np(eg), eo)):
+        assert _field_err(a, b) < STEP_TOL
