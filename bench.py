@@ -43,6 +43,10 @@ WORKLOADS = {
     "tg2d_8_q2": dict(dim=2, n=8, order=2, q1=4, jitter=0.0, t_end=0.02, cfl=0.5,
                       desc="2D Taylor-Green, 8^2 quads, Q2/Q1, 4^2 Gauss points"),
 }
+# DRAM bytes (read + write) of one launch of the roofline kernel, from one ncu
+# capture of the unchanged kernel (profiles/k_cg_tg3d24_q2_fp64.md); None where
+# no capture of the current kernel exists.
+TRAFFIC = {("tg3d_24_q2", "fp64"): 21185280}
 METRIC = "MDOF/s of PA force+mass path (RK2-average step, H1 vector DOFs per second)"
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -189,7 +193,8 @@ def run_ours(args):
     K = args.steps
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    cg_iters = []
+    iters_before = ctx.read_step_info(info).cg_iters_total
+    ctx.timing_enable(True)          # events around each solver launch, on the step's stream
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -203,9 +208,12 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
+    solver_ms, solver_launches = ctx.timing_read()
+    ctx.timing_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     t_local = sum(step_ms) / 1e3
     si = ctx.read_step_info(info)
+    timed_iters = int(si.cg_iters_total - iters_before)
     status = ctx.sync_status()
     t_max = max_over_ranks(t_local, world, "cuda")
     value = job_rate(sz.nv, K, world, t_max)
@@ -247,13 +255,27 @@ def run_ours(args):
         "force_mult": {"ms": t_f, "tflops": W["force_flops"] / (t_f * 1e-3) / 1e12},
         "force_mult_t": {"ms": t_ft, "tflops": W["force_t_flops"] / (t_ft * 1e-3) / 1e12},
     }
+    # Roofline of the dominant kernel, measured live over the timed steps: the
+    # library's event pairs around each solver launch (same stream) give its
+    # time; algorithmic FLOPs = iterations x CG-iteration FLOPs + one matvec per solve.
+    # With fp32_ir the iterations are the FP32 inner ones and the peak is the FP32 one.
+    timed_flops = timed_iters * W["cg_iter_flops"] + solver_launches * W["mass_flops"]
+    achieved = timed_flops / (solver_ms * 1e-3) / 1e12 if solver_ms > 0 else 0.0
+    peak = peak64 if args.precision == "fp64" else peak32
     roofline = {"bound": "alu", "kernel": "k_cg (persistent Jacobi-PCG on the PA mass operator)"
                 if args.precision == "fp64" else "k_cg_ir (FP32 PCG under FP64 refinement)",
-                "achieved": kernels["mass_cg"]["tflops"], "peak": peak64, "unit": "TFLOP/s",
-                "frac": kernels["mass_cg"]["tflops"] / peak64 if peak64 > 0 else None, "traffic": None,
-                "peak_source": "measured FP64 FMA-chain probe (paper_2112_07075_b300/probe/alu_peak.cu), "
-                               "same run; derived 148 SM x 2 DFMA/clk x 2 flop x clock",
-                "flops_per_launch": cg_flops, "fp32_peak_tflops": peak32}
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak > 0 else None,
+                "traffic": TRAFFIC.get((args.workload, args.precision)),
+                "peak_source": ("measured FP64 FMA-chain probe (paper_2112_07075_b300/probe/alu_peak.cu), "
+                                "same run; derived 148 SM x 2 DFMA/clk x 2 flop x clock")
+                if args.precision == "fp64" else
+                "measured FP32 FMA-chain probe (paper_2112_07075_b300/probe/alu_peak.cu), same run",
+                "launches": solver_launches, "launch_ms_avg": solver_ms / max(1, solver_launches),
+                "flops_per_launch": timed_flops / max(1, solver_launches),
+                "iters_per_launch": timed_iters / max(1, solver_launches),
+                "share_of_step": solver_ms / max(1e-9, sum(step_ms)),
+                "fp32_peak_tflops": peak32}
 
     # ---- end-to-end through the public API with host buffers
     e2e = None

@@ -119,6 +119,8 @@ typedef struct {
   int cg_iters[2];    /* CG iterations of the last step's two mass solves */
   int status;         /* LH_OK or the first device-side error of the last step */
   int steps;          /* steps taken with this record */
+  long long cg_iters_total; /* sum of cg_iters over all steps taken with this record
+                               (lh_rk2avg_step only; the batch step leaves it alone) */
 } lh_step_info;
 
 typedef struct lh_ctx lh_ctx;
@@ -210,6 +212,18 @@ lh_status lh_energy_solve(lh_ctx *ctx, const double *rhs, double *out, lh_stream
  * warm-started from the previous solve's acceleration. */
 lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt,
                          double rel_tol, int max_it, lh_step_info *info, lh_stream_t stream);
+
+/* Solver timing probe (measurement support; no counterpart in the paper).
+ * lh_timing_enable(ctx, 1) makes every later mass solve of this context
+ * (lh_mass_cg and the two solves inside lh_rk2avg_step) record a pair of CUDA
+ * events on its stream around the solver launch; up to 64 solves are kept.
+ * lh_timing_read waits for the recorded events, returns the summed solver time
+ * in milliseconds and the number of solves since the previous read, and starts
+ * a new record. Leave timing disabled while capturing a CUDA graph (the events
+ * would become capture dependencies, not timestamps). Returns LH_ERR_ARG on NULL
+ * arguments, LH_ERR_CUDA if an event call fails. */
+lh_status lh_timing_enable(lh_ctx *ctx, int enable);
+lh_status lh_timing_read(lh_ctx *ctx, double *solver_ms, int *solves);
 
 /* ---------------------------------------------------------------------------
  * Batching form: many independent problems advanced together.

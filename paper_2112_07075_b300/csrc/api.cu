@@ -151,6 +151,7 @@ __global__ void k_to_float(size_t n, const double *__restrict__ a, float *__rest
 __global__ void k_step_finish(lh_step_info *info, const int *status, int has_source) {
   info->t += info->dt;
   info->steps += 1;
+  info->cg_iters_total += (long long)info->cg_iters[0] + info->cg_iters[1];
   info->status = *status;
   if (!has_source) info->energy_src = 0.0;
 }
@@ -192,6 +193,8 @@ extern "C" {
 void lh_destroy(lh_ctx *ctx) {
   if (!ctx) return;
   lh::learn_free(ctx->learn);
+  for (cudaEvent_t &ev : ctx->tev)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->arena) cudaFree(ctx->arena);
   delete ctx;
 }
@@ -490,8 +493,8 @@ constexpr double kInnerTol = 1e-5;   // FP32 inner solve: relative residual per 
 constexpr int kMaxOuter = 40;
 constexpr int kMaxInner = 200;
 
-static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
-                         int *iters_out, double *relres_out, cudaStream_t s) {
+static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
+                           int *iters_out, double *relres_out, cudaStream_t s) {
   if (c->prm.precision == LH_PRECISION_FP32_IR) {
     CgIrArgs a{};
     a.mesh = c->mesh;
@@ -545,6 +548,50 @@ static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int 
   const cudaError_t e = c->ops->cg(a, c->grid_cg, s);
   if (e != cudaSuccess) return fail(c, LH_ERR_CUDA, std::string("cg launch: ") + cudaGetErrorString(e));
   return check_launch(c, "cg");
+}
+
+// Every mass solve goes through here; with the timing probe on, a pair of events
+// brackets the solver launch on its stream.
+static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
+                         int *iters_out, double *relres_out, cudaStream_t s) {
+  const bool rec = c->timing && c->timing_n < lh_ctx::kTimingPairs;
+  if (rec && cudaEventRecord(c->tev[2 * c->timing_n], s) != cudaSuccess)
+    return fail(c, LH_ERR_CUDA, "timing event record");
+  const lh_status st = cg_launch(c, b, x, tol, max_it, info, iters_out, relres_out, s);
+  if (st != LH_OK) return st;
+  if (rec) {
+    if (cudaEventRecord(c->tev[2 * c->timing_n + 1], s) != cudaSuccess)
+      return fail(c, LH_ERR_CUDA, "timing event record");
+    ++c->timing_n;
+  }
+  return LH_OK;
+}
+
+lh_status lh_timing_enable(lh_ctx *ctx, int enable) {
+  if (!ctx) return LH_ERR_ARG;
+  if (enable && !ctx->tev[0]) {
+    for (cudaEvent_t &ev : ctx->tev)
+      if (cudaEventCreate(&ev) != cudaSuccess) return fail(ctx, LH_ERR_CUDA, "timing event create");
+  }
+  ctx->timing = enable != 0;
+  ctx->timing_n = 0;
+  return LH_OK;
+}
+
+lh_status lh_timing_read(lh_ctx *ctx, double *solver_ms, int *solves) {
+  if (!ctx || !solver_ms || !solves) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  double total = 0.0;
+  for (int i = 0; i < ctx->timing_n; ++i) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(ctx->tev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, ctx->tev[2 * i], ctx->tev[2 * i + 1]) != cudaSuccess)
+      return fail(ctx, LH_ERR_CUDA, "timing event read");
+    total += ms;
+  }
+  *solver_ms = total;
+  *solves = ctx->timing_n;
+  ctx->timing_n = 0;
+  return LH_OK;
 }
 
 lh_status lh_mass_cg(lh_ctx *ctx, const double *b, double *x, double rel_tol, int max_it, lh_cg_info *info,

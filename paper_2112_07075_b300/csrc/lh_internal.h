@@ -184,6 +184,11 @@ struct lh_ctx {
   void *bar = nullptr;   // lh::GridBarrier
   int *dstatus = nullptr;
   lh_learn *learn = nullptr;   // learned-form state (lh_learn_attach), or NULL
+  // solver timing probe (lh_timing_enable): event pairs around solver launches
+  static constexpr int kTimingPairs = 64;
+  bool timing = false;
+  int timing_n = 0;
+  cudaEvent_t tev[2 * kTimingPairs] = {};
   std::string err = "no error";
 };
 

@@ -29,7 +29,7 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy",
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_learn_attach",
-            "lh_learn_stats", "lh_selftest_barrier_timeout"]
+            "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read"]
 
 
 class LhParams(ctypes.Structure):
@@ -53,7 +53,7 @@ class LhStepInfo(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("t_end", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dt_est", ctypes.c_double), ("energy_src", ctypes.c_double),
                 ("cg_rel_res", ctypes.c_double * 2), ("cg_iters", ctypes.c_int * 2),
-                ("status", ctypes.c_int), ("steps", ctypes.c_int)]
+                ("status", ctypes.c_int), ("steps", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong)]
 
 
 _lib = None
@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mlp_last_error": (ctypes.c_char_p, [P]),
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
         "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
+        "lh_timing_enable": (I, [P, I]),
+        "lh_timing_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
     }
@@ -258,6 +260,16 @@ class Context:
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))
+
+    def timing_enable(self, enable: bool = True) -> None:
+        """Record CUDA events around every later mass-solver launch (lh_timing_enable)."""
+        self._check(self.lib.lh_timing_enable(self.h, 1 if enable else 0))
+
+    def timing_read(self):
+        """(summed solver milliseconds, number of solves) since the previous read."""
+        ms, n = ctypes.c_double(0.0), ctypes.c_int(0)
+        self._check(self.lib.lh_timing_read(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
 
 class Batch:
