@@ -67,7 +67,7 @@ typedef enum {
 
 typedef enum { LH_PROBLEM_TAYLOR_GREEN = 0, LH_PROBLEM_GRESHO = 1 } lh_problem;
 typedef enum { LH_SOURCE_NONE = 0, LH_SOURCE_TAYLOR_GREEN_2D = 1 } lh_source;
-typedef enum { LH_PRECISION_FP64 = 0, LH_PRECISION_FP32_IR = 1 } lh_precision;
+typedef enum { LH_PRECISION_FP64 = 0, LH_PRECISION_FP32_IR = 1, LH_PRECISION_BF16TC_IR = 2 } lh_precision;
 
 typedef struct {
   int dim;                  /* 2 or 3 */
@@ -84,7 +84,11 @@ typedef struct {
                                lh_rk2avg_step): LH_PRECISION_FP64 = FP64 Jacobi PCG;
                                LH_PRECISION_FP32_IR = FP32 Jacobi PCG inner solves (FP32
                                mass data, vectors, contractions) under FP64 iterative
-                               refinement (FP64 residual b - M x, norms, x update) */
+                               refinement (FP64 residual b - M x, norms, x update);
+                               LH_PRECISION_BF16TC_IR = the same refinement with the inner
+                               element contractions on the tensor cores (BF16 hi/lo split
+                               operands, FP32 accumulation; dim 3, order >= 3,
+                               q1^3 <= 256, else lh_setup returns LH_ERR_UNSUPPORTED) */
 } lh_params;
 
 /* Sizes of a context's spaces. */
@@ -186,15 +190,23 @@ lh_status lh_force_mult_t(lh_ctx *ctx, const double *v, double *out, lh_stream_t
  * x, y: DEVICE [dim][N_H1] (must not alias); no boundary conditions applied. */
 lh_status lh_mass_mult(lh_ctx *ctx, const double *x, double *y, lh_stream_t stream);
 
+/* Velocity mass action with the tensor-core element operator of
+ * LH_PRECISION_BF16TC_IR (the operator its inner solves use): y = M x in FP32,
+ * x masked to the free DOFs (constrained DOFs count as 0), no boundary conditions
+ * on y. x, y: DEVICE FP32 [dim][N_H1], must not alias. Returns LH_ERR_UNSUPPORTED
+ * for contexts of another precision. */
+lh_status lh_mass_mult_tc(lh_ctx *ctx, const float *x, float *y, lh_stream_t stream);
+
 /* Velocity mass solve (Eq. 14, "inversion of a global CG mass matrix", Section 6):
  * Jacobi-preconditioned CG for M_v x = b on the free DOFs (v.n = 0 on the box
  * faces; x is set to 0 on constrained DOFs and b is ignored there), stopping when
  * the FP64 residual satisfies ||b - M x||_2 <= rel_tol ||b||_2. x: in = initial
  * guess, out = solution. b, x: DEVICE [dim][N_H1]. info: DEVICE lh_cg_info or NULL.
  * With the context's precision LH_PRECISION_FP64, max_it bounds the CG iterations;
- * with LH_PRECISION_FP32_IR each refinement step runs an FP32 PCG to a relative
- * residual of 1e-5 (at most 200 iterations), at most 40 steps are taken, max_it
- * bounds the total FP32 iterations, and info->iters reports that total.
+ * with LH_PRECISION_FP32_IR (LH_PRECISION_BF16TC_IR) each refinement step runs an
+ * FP32 PCG to a relative residual of 1e-5 (1e-4) (at most 200 iterations), at most
+ * 40 steps are taken, max_it bounds the total inner iterations, and info->iters
+ * reports that total.
  * One persistent cooperative launch; convergence is decided on the device. */
 lh_status lh_mass_cg(lh_ctx *ctx, const double *b, double *x, double rel_tol, int max_it,
                      lh_cg_info *info, lh_stream_t stream);

@@ -242,6 +242,9 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   LH_CUDA(c, cudaGetDevice(&dev));
   LH_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
   const Ops &o = *c->ops;
+  const bool tcf = prm->precision == LH_PRECISION_BF16TC_IR;
+  if (tcf && !o.cg_tc)
+    return fail(c, LH_ERR_UNSUPPORTED, "the tensor-core precision form needs dim 3, order >= 3 and q1^3 <= 256");
   const size_t smems[] = {o.smem_qdata, o.smem_force, o.smem_force_t, o.smem_mass, o.smem_cg,
                           o.smem_geom,  o.smem_diag,  o.smem_emass,   o.smem_init_e, o.smem_cg_ir};
   void *kerns[] = {o.k_qdata, o.k_force, o.k_force_t, o.k_mass,   o.k_cg,
@@ -260,6 +263,17 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
     LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, o.k_cg_ir, o.threads_cg, o.smem_cg_ir));
     if (occ2 < 1) return fail(c, LH_ERR_CUDA, "IR CG kernel cannot be resident");
     c->grid_cg_ir = std::min(std::min(occ2, 2) * c->sms, want);
+    if (tcf) {   // one CTA per SM (shared memory), all SMs: tiles are spread round-robin
+      LH_CUDA(c, cudaFuncSetAttribute(o.k_cg_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_cg_tc));
+      int occ3 = 0;
+      LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, o.k_cg_tc, o.threads_cg_tc, o.smem_cg_tc));
+      if (occ3 < 1) return fail(c, LH_ERR_CUDA, "tensor-core CG kernel cannot be resident");
+      // no more blocks than the work (tiles of 128 rows, node sweeps): the partial-sum
+      // scratch below is sized for this grid
+      const int tiles = (int)((3 * (size_t)m.ne + 127) / 128);
+      c->grid_cg_tc = std::min(c->sms, std::max(tiles, grid_for(c->nv / c->dim, o.threads_cg_tc, 1 << 30)));
+      LH_CUDA(c, cudaFuncSetAttribute(o.k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_cg_tc));
+    }
   }
   c->grid_node = grid_for(c->nv, kNodeThreads, 8 * c->sms * 8);
 
@@ -267,8 +281,9 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   const size_t NE = m.ne, NQ = c->nq, NH1 = m.nh1, NV = c->nv;
   const int tablen = table_length(p, q1);
   const size_t nverts = (size_t)(m.nx + 1) * (m.ny + 1) * (dim == 3 ? m.nz + 1 : 1);
-  const size_t npart = 8 * (size_t)std::max(c->grid_elem, std::max(c->grid_cg, c->grid_cg_ir));
-  const bool ir = prm->precision == LH_PRECISION_FP32_IR;
+  const size_t npart =
+      8 * (size_t)std::max(std::max(c->grid_elem, c->grid_cg_tc), std::max(c->grid_cg, c->grid_cg_ir));
+  const bool ir = prm->precision != LH_PRECISION_FP64;
   const size_t nf = ir ? 1 : 0;   // FP32 buffers only for the precision form
   struct Item { double **ptr; size_t n; };
   std::vector<Item> items = {
@@ -282,7 +297,8 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
       {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
       {(double **)&c->ap32, nf * (NV + 1) / 2},       {(double **)&c->d32, nf * (NV + 1) / 2},
-      {(double **)&c->evec32, nf * (NE * dim * c->nd + 1) / 2}};
+      {(double **)&c->evec32, nf * (NE * dim * c->nd + 1) / 2},
+      {(double **)&c->kimg, tcf ? (o.tc_img_bytes + 7) / 8 : 0}};
   size_t bytes = 0;
   for (auto &it : items) bytes += (it.n * sizeof(double) + 255) / 256 * 256;
   const size_t ctl_bytes = 256;
@@ -312,6 +328,11 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
     return fail(c, LH_ERR_ARG, ex.what());
   }
   LH_CUDA(c, cudaMemcpy(c->tab, tab.data(), tablen * sizeof(double), cudaMemcpyHostToDevice));
+  if (tcf) {   // B = the table's first block, [q1][p+1]
+    std::vector<unsigned short> img(o.tc_img_bytes / 2);
+    o.tc_image(tab.data(), img.data());
+    LH_CUDA(c, cudaMemcpy(c->kimg, img.data(), o.tc_img_bytes, cudaMemcpyHostToDevice));
+  }
   LH_CUDA(c, cudaMemcpy(c->verts, prm->vertices, nverts * dim * sizeof(double), cudaMemcpyHostToDevice));
   Zs z{};
   gll_nodes(p, z.z);
@@ -369,7 +390,8 @@ lh_status lh_setup(const lh_params *prm, const double *rho0_q, lh_ctx **out) {
     return fail(nullptr, LH_ERR_ARG, "unknown source");
   if (prm->source == LH_SOURCE_TAYLOR_GREEN_2D && prm->dim != 2)
     return fail(nullptr, LH_ERR_ARG, "the Taylor-Green source is 2D only");
-  if (prm->precision != LH_PRECISION_FP64 && prm->precision != LH_PRECISION_FP32_IR)
+  if (prm->precision != LH_PRECISION_FP64 && prm->precision != LH_PRECISION_FP32_IR &&
+      prm->precision != LH_PRECISION_BF16TC_IR)
     return fail(nullptr, LH_ERR_ARG, "unknown precision");
   lh_ctx *c = new lh_ctx();
   const lh_status s = setup_impl(c, prm, rho0_q);
@@ -490,12 +512,14 @@ lh_status lh_mass_mult(lh_ctx *ctx, const double *x, double *y, lh_stream_t stre
 }
 
 constexpr double kInnerTol = 1e-5;   // FP32 inner solve: relative residual per refinement step
+constexpr double kInnerTolTc = 1e-4; // tensor-core inner solve (BF16 hi/lo operator, ~1e-6 accurate)
 constexpr int kMaxOuter = 40;
 constexpr int kMaxInner = 200;
 
 static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
                            int *iters_out, double *relres_out, cudaStream_t s) {
-  if (c->prm.precision == LH_PRECISION_FP32_IR) {
+  if (c->prm.precision == LH_PRECISION_FP32_IR || c->prm.precision == LH_PRECISION_BF16TC_IR) {
+    const bool tcf = c->prm.precision == LH_PRECISION_BF16TC_IR;
     CgIrArgs a{};
     a.mesh = c->mesh;
     a.tab = c->tab;
@@ -518,11 +542,12 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
     a.iters_out = iters_out;
     a.relres_out = relres_out;
     a.tol = tol;
-    a.inner_tol = kInnerTol;
+    a.inner_tol = tcf ? kInnerTolTc : kInnerTol;
     a.max_it = max_it;
     a.max_outer = kMaxOuter;
     a.max_inner = kMaxInner;
-    const cudaError_t e = c->ops->cg_ir(a, c->grid_cg_ir, s);
+    a.kimg = c->kimg;
+    const cudaError_t e = tcf ? c->ops->cg_tc(a, c->grid_cg_tc, s) : c->ops->cg_ir(a, c->grid_cg_ir, s);
     if (e != cudaSuccess) return fail(c, LH_ERR_CUDA, std::string("cg_ir launch: ") + cudaGetErrorString(e));
     return check_launch(c, "cg_ir");
   }
@@ -592,6 +617,26 @@ lh_status lh_timing_read(lh_ctx *ctx, double *solver_ms, int *solves) {
   *solves = ctx->timing_n;
   ctx->timing_n = 0;
   return LH_OK;
+}
+
+lh_status lh_mass_mult_tc(lh_ctx *ctx, const float *x, float *y, lh_stream_t stream) {
+  if (!ctx || !x || !y) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (ctx->prm.precision != LH_PRECISION_BF16TC_IR)
+    return fail(ctx, LH_ERR_UNSUPPORTED, "context was not set up with LH_PRECISION_BF16TC_IR");
+  if (x == y) return fail(ctx, LH_ERR_ARG, "x and y must not alias");
+  CgIrArgs a{};
+  a.mesh = ctx->mesh;
+  a.tab = ctx->tab;
+  a.mq32 = ctx->mq32;
+  a.invdiag32 = ctx->invdiag32;
+  a.d32 = const_cast<float *>(x);   // read only (masked source vector)
+  a.evec32 = ctx->evec32;
+  a.ap32 = y;
+  a.status = ctx->dstatus;
+  a.kimg = ctx->kimg;
+  const cudaError_t e = ctx->ops->tc_apply(a, ctx->grid_cg_tc, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(ctx, LH_ERR_CUDA, std::string("tensor-core mass action: ") + cudaGetErrorString(e));
+  return check_launch(ctx, "tensor-core mass action");
 }
 
 lh_status lh_mass_cg(lh_ctx *ctx, const double *b, double *x, double rel_tol, int max_it, lh_cg_info *info,

@@ -90,6 +90,7 @@ struct CgIrArgs {
   double *relres_out;
   double tol, inner_tol;
   int max_it, max_outer, max_inner;
+  const void *kimg;   // tensor-core form: shared-memory image of the BF16 interpolation matrix
 };
 
 struct GeomArgs {
@@ -136,6 +137,17 @@ struct Ops {
   void (*init_e)(const InitEArgs &, int grid, cudaStream_t);
   void (*gather)(const MeshDesc &, const double *evec, int C, double *out, double scale, const double *mask,
                  int grid, int threads, cudaStream_t);
+  // tensor-core inner solver of the precision form (NULL where the family has none)
+  void *k_cg_tc;
+  size_t smem_cg_tc;
+  int threads_cg_tc;
+  size_t tc_img_bytes;
+  cudaError_t (*cg_tc)(CgIrArgs &, int grid, cudaStream_t);
+  void (*tc_image)(const double *B, unsigned short *img);   // host: B = 1D table [q1][p+1]
+  void *k_tc_apply;
+  // M x with the tensor-core element operator: x = a.d32 (free DOFs), E-vector in
+  // a.evec32, node sums in a.ap32
+  cudaError_t (*tc_apply)(CgIrArgs &, int grid, cudaStream_t);
 };
 
 const Ops *find_ops_2d(int p, int q1);
@@ -179,7 +191,8 @@ struct lh_ctx {
          *eh = nullptr, *partials = nullptr;
   float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
         *evec32 = nullptr;
-  int grid_cg_ir = 0;
+  int grid_cg_ir = 0, grid_cg_tc = 0;
+  unsigned short *kimg = nullptr;   // tensor-core form: BF16 image of the interpolation matrix
   unsigned int *counter = nullptr;
   void *bar = nullptr;   // lh::GridBarrier
   int *dstatus = nullptr;

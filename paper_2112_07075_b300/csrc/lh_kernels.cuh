@@ -968,10 +968,35 @@ struct Family {
     double *u = R, *S = u + CXC * ND, *uq = S + MC_S, *y = uq + CXC * NQ;                 // FP64 view
     float *tb = (float *)R, *tbt = tb + Q * D, *uf = tbt + Q * D, *Sf = uf + CXF * ND;    // FP32 view
     float *uqf = Sf + MF_S, *yf = uqf + CXF * NQ;
+    __shared__ int s_eb[NB_EB];
+    load_tab(st, a.tab);
+    __syncthreads();
+    cg_ir_core<false>(
+        a, st, u, S, uq, y, red, s_eb,
+        [&]() {   // FP32 copies of the 1D tables (the FP64 sweep reuses this space)
+          for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x)
+            tb[k] = (float)(k < Q * D ? st[oB + k] : st[oBt + k - Q * D]);
+          __syncthreads();
+        },
+        [&](float beta) {
+          sweep_matvec_f<3>(a.mesh, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32,
+                            a.p32, 0.0f, beta, a.evec32);
+          return true;
+        });
+  }
+
+  // The refinement loop shared by the CUDA-core (body_cg_ir) and tensor-core
+  // (lh_tc.cuh) inner solvers: inner_begin() runs before each inner solve,
+  // inner_sweep(beta) writes the FP32 E-vector of M p_new (false: a bounded
+  // device wait gave up). st/u/S/uq/y: FP64 sweep space; RELOAD_TAB: the
+  // FP64 tables share space with the inner sweep and are reloaded per refinement.
+  template <bool RELOAD_TAB, class Begin, class Sweep>
+  static __device__ __forceinline__ void cg_ir_core(const CgIrArgs &a, double *st, double *u, double *S, double *uq,
+                                                    double *y, double *red, int *s_eb, Begin &&inner_begin,
+                                                    Sweep &&inner_sweep) {
     float *redf = (float *)red;
     __shared__ double s_sc[4];
     __shared__ float s_f[4];
-    __shared__ int s_eb[NB_EB];
     const MeshDesc &m = a.mesh;
     const int G = gridDim.x;
     const int nh1 = m.nh1;
@@ -981,8 +1006,6 @@ struct Family {
     GridBarrier *bar = (GridBarrier *)a.bar;
     unsigned long long nbar = 0;
     auto sync = [&]() { ++nbar; return grid_sync(bar, nbar * (unsigned long long)G, a.status); };
-    load_tab(st, a.tab);
-    __syncthreads();
     int outer = 0;
     auto finish = [&](int iters, int status, double rr, double bb) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1020,6 +1043,10 @@ struct Family {
     double bb = -1.0;
     int inner_total = 0;
     for (;; ++outer) {
+      if constexpr (RELOAD_TAB) {
+        load_tab(st, a.tab);
+        __syncthreads();
+      }
       // ---- O-A: FP64 E-vector of M x (x masked to the free DOFs)
       sweep_matvec<0, double>(m, s_eb, st + oB, st + oBt, u, S, uq, y, a.mq, a.invdiag, a.x, a.x, a.x, a.x, 0.0,
                               0.0, a.evec);
@@ -1090,9 +1117,7 @@ struct Family {
       // ---- inner FP32 PCG (standard form, exact dot products, three grid barriers
       //      per iteration: in FP32 the scalar recurrence of the FP64 solver
       //      loses too many digits when a step shrinks (r, z) strongly)
-      for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x)
-        tb[k] = (float)(k < Q * D ? st[oB + k] : st[oBt + k - Q * D]);
-      __syncthreads();
+      inner_begin();
       float rr = s_f[0], rz = s_f[1], rz_old = rz;
       // relative reduction of this inner solve: inner_tol, or less when a smaller
       // step reaches the FP64 tolerance (0.1 safety factor): a good initial guess
@@ -1106,9 +1131,8 @@ struct Family {
         const float beta = it == 0 ? 0.0f : rz / rz_old;
         rz_old = rz;
         // E: FP32 E-vector of M p_new, p_new = invdiag r + beta p
-        sweep_matvec_f<3>(m, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32, a.p32,
-                          0.0f, beta, a.evec32);
-        if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        const bool swept = inner_sweep(beta);
+        if (!swept || !sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
         {  // q = M p_new gathered, p = p_new, p.q
           float acc[5] = {0, 0, 0, 0, 0};
           for (int g = gtid; g < nh1; g += gstride) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "lh_kernels.cuh"
+#include "lh_tc.cuh"
 
 namespace lh {
 
@@ -45,6 +46,46 @@ struct OpsBuilder {
     return cudaLaunchCooperativeKernel((const void *)k_cg_ir<DIM, P, Q>, dim3(grid), dim3(F::TC), args,
                                        F::cg_ir_smem(), s);
   }
+  static constexpr bool kTc = TcTraits<DIM, P, Q>::on;
+  static cudaError_t cg_tc(CgIrArgs &a, int grid, cudaStream_t s) {
+    if constexpr (kTc) {
+      void *args[] = {&a};
+      cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), s);
+      if (e != cudaSuccess) return e;
+      return cudaLaunchCooperativeKernel((const void *)k_cg_tc<P, Q>, dim3(grid), dim3(TcMass<P, Q>::THREADS), args,
+                                         TcMass<P, Q>::SMEM, s);
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  static cudaError_t tc_apply(CgIrArgs &a, int grid, cudaStream_t s) {
+    if constexpr (kTc) {
+      k_tc_apply<P, Q><<<grid, TcMass<P, Q>::THREADS, TcMass<P, Q>::SMEM, s>>>(a);
+      k_gather_f32<P + 1><<<grid * 4, 256, 0, s>>>(a.mesh, a.evec32, a.ap32);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  static void *tc_apply_kernel() {
+    if constexpr (kTc) return (void *)k_tc_apply<P, Q>;
+    else return nullptr;
+  }
+  static void *tc_kernel() {
+    if constexpr (kTc) return (void *)k_cg_tc<P, Q>;
+    else return nullptr;
+  }
+  static size_t tc_smem() {
+    if constexpr (kTc) return TcMass<P, Q>::SMEM;
+    else return 0;
+  }
+  static size_t tc_img_bytes() {
+    if constexpr (kTc) return TcLayout<P, Q>::IMG;
+    else return 0;
+  }
+  static void tc_image(const double *B, unsigned short *img) {
+    if constexpr (kTc) tc_build_image<P, Q>(B, img);
+  }
   static void geom(const GeomArgs &a, int grid, cudaStream_t s) {
     k_geom<DIM, P, Q><<<grid, F::THREADS, F::geom_smem(), s>>>(a);
   }
@@ -69,7 +110,10 @@ struct OpsBuilder {
                             (void *)k_cg<DIM, P, Q>, (void *)k_geom<DIM, P, Q>, (void *)k_diag<DIM, P, Q>, (void *)k_emass<DIM, P, Q>,
                             (void *)k_init_e<DIM, P, Q>, (void *)k_cg_ir<DIM, P, Q>,
                             &qdata, &force, &force_t, &mass, &cg, &cg_ir, &geom, &diag, &emass, &init_e,
-                            &gather};
+                            &gather,
+                            tc_kernel(), tc_smem(), kTc ? 512 : 0, tc_img_bytes(),
+                            kTc ? &cg_tc : nullptr, kTc ? &tc_image : nullptr,
+                            tc_apply_kernel(), kTc ? &tc_apply : nullptr};
     return &ops;
   }
 };

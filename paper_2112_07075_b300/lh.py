@@ -21,7 +21,7 @@ LH_OK, LH_ERR_ARG, LH_ERR_CUDA, LH_ERR_OOM, LH_ERR_INVERTED, LH_ERR_NOT_CONVERGE
 STATUS_NAMES = ["ok", "argument", "cuda", "out of memory", "inverted", "not converged", "timeout", "unsupported"]
 PROBLEMS = {"taylor_green": 0, "gresho": 1}
 SOURCES = {"none": 0, "tg2d": 1}
-PRECISIONS = {"fp64": 0, "fp32_ir": 1}
+PRECISIONS = {"fp64": 0, "fp32_ir": 1, "bf16tc_ir": 2}
 
 EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_status", "lh_init_state",
             "lh_update_qdata", "lh_copy_qdata", "lh_force_mult", "lh_force_mult_t", "lh_mass_mult",
@@ -29,7 +29,7 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy",
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_learn_attach",
-            "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read"]
+            "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc"]
 
 
 class LhParams(ctypes.Structure):
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
         "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
         "lh_timing_enable": (I, [P, I]),
+        "lh_mass_mult_tc": (I, [P, VP, VP, VP]),
         "lh_timing_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
@@ -246,6 +247,10 @@ class Context:
 
     def mass_mult(self, x, y):
         self._check(self.lib.lh_mass_mult(self.h, _ptr(x), _ptr(y), _stream()))
+
+    def mass_mult_tc(self, x, y):
+        """y = M x with the tensor-core element operator (FP32 tensors; bf16tc_ir contexts)."""
+        self._check(self.lib.lh_mass_mult_tc(self.h, _ptr(x), _ptr(y), _stream()))
 
     def mass_cg(self, b, x, rel_tol=1e-12, max_it=1000, info=None):
         self._check(self.lib.lh_mass_cg(self.h, _ptr(b), _ptr(x), float(rel_tol), int(max_it), _ptr(info),
