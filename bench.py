@@ -404,6 +404,12 @@ def forms_report(flush, steps=3, warmup=1):
         rep[wl_name] = {"fp64": f64, "fp32_ir": f32, "speedup": f64["ms_per_step"] / f32["ms_per_step"],
                         "max_rel_field_diff_vs_fp64_gpu": err, "steps": warmup + steps,
                         "note": "same initial state, CFL steps from t=0; per-step CUDA-event time, L2 flushed"}
+        if WORKLOADS[wl_name]["order"] >= 3:   # tensor-core inner operator (order >= 3)
+            ftc, stc = measure_form(wl_name, "bf16tc_ir", steps, warmup, flush)
+            rep[wl_name]["bf16tc_ir"] = ftc
+            rep[wl_name]["bf16tc_ir"]["speedup_vs_fp64"] = f64["ms_per_step"] / ftc["ms_per_step"]
+            rep[wl_name]["bf16tc_ir"]["max_rel_field_diff_vs_fp64_gpu"] = max(
+                float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(stc, s64))
     return rep
 
 
@@ -527,10 +533,11 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
            "config": f"eval {eval_n}^3 Q3 seeds 9,10 x {eval_steps} steps; train {train_seeds} seeds x "
                      f"{train_steps} steps at {train_n}^3 (reduced from 2000 steps per seed)"}
     finals = {}
-    for mode in ("fp64", "fp64+learned", "fp32_ir", "fp32_ir+learned"):
+    modes = ("fp64", "fp64+learned", "fp32_ir", "fp32_ir+learned", "bf16tc_ir", "bf16tc_ir+learned")
+    for mode in modes:
         ms, its, used, preds, ratios = [], [], 0, 0, []
         for si, V in enumerate(Ve):
-            c = Context(3, eval_n, V, 3, 6, precision="fp64" if mode.startswith("fp64") else "fp32_ir")
+            c = Context(3, eval_n, V, 3, 6, precision=mode.split("+")[0])
             if mode.endswith("learned"):
                 learn_attach(c, net, 2)
             xs, vs, es = c.init_state()
@@ -559,7 +566,7 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
             out[mode]["predictions"] = preds
             out[mode]["mean_initial_residual_ratio_learned_vs_previous"] = statistics.mean(ratios)
     base = finals["fp64"]
-    for mode in ("fp64+learned", "fp32_ir", "fp32_ir+learned"):
+    for mode in modes[1:]:
         out[mode]["max_rel_field_diff_vs_fp64_gpu"] = max(
             float(_np.linalg.norm(a - b) / _np.linalg.norm(b)) for a, b in zip(finals[mode], base))
         out[mode]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out[mode]["ms_per_step"]
@@ -638,7 +645,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "bf16tc_ir"],
                     help="mass-solve precision of the main arm (the headline workload is FP64)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -893,20 +893,35 @@ struct Family {
       sweep_matvec<3, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.x, a.r, a.ap, a.p, 0.0, beta,
                               a.evec);
       if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
-      {  // q = M p_new, p = p_new, p.q
+      {  // q = M p_new, p = p_new, p.q (all loads of a node before any use)
         double acc[1] = {0.0};
         for (int g = gtid; g < nh1; g += gstride) {
-          int off[1 << DIM];
+          int off[1 << DIM] = {};
           const int n = node_copies<DIM, D>(m, g, DIM, off);
+          double idg[DIM], pv[DIM], rv[DIM];
+#pragma unroll
           for (int c = 0; c < DIM; ++c) {
             const int k = c * nh1 + g;
-            const double idg = a.invdiag[k];
-            double qv = 0.0, pn = 0.0;
-            if (idg != 0.0) {
-              qv = a.evec[off[0] + c * ND];
-              for (int j = 1; j < n; ++j) qv += a.evec[off[j] + c * ND];
-              pn = fma(beta, a.p[k], idg * a.r[k]);
+            idg[c] = __ldg(a.invdiag + k);
+            pv[c] = a.p[k];
+            rv[c] = a.r[k];
+          }
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {   // one component's copies at a time (register budget)
+            const int k = c * nh1 + g;
+            double ev[1 << DIM];
+#pragma unroll
+            for (int j = 0; j < (1 << DIM); ++j) ev[j] = j < n ? a.evec[off[j] + c * ND] : 0.0;
+            double qv = ev[0];
+#pragma unroll
+            for (int j = 1; j < (1 << DIM); ++j)
+              if (j < n) qv += ev[j];
+            double pn = 0.0;
+            if (idg[c] != 0.0) {
+              pn = fma(beta, pv[c], idg[c] * rv[c]);
               acc[0] = fma(pn, qv, acc[0]);
+            } else {
+              qv = 0.0;
             }
             a.ap[k] = qv;
             a.p[k] = pn;
@@ -922,16 +937,30 @@ struct Family {
       }
       __syncthreads();
       const double alpha = s_sc[4];
-      {  // x += alpha p, r -= alpha q, r.r, r.z
+      {  // x += alpha p, r -= alpha q, r.r, r.z (two DOFs per step, loads first)
         double acc[2] = {0.0, 0.0};
-        for (int k = gtid; k < DIM * nh1; k += gstride) {
-          const double idg = a.invdiag[k];
-          if (idg != 0.0) {
-            a.x[k] = fma(alpha, a.p[k], a.x[k]);
-            const double rv = fma(-alpha, a.ap[k], a.r[k]);
-            a.r[k] = rv;
-            acc[0] = fma(rv, rv, acc[0]);
-            acc[1] = fma(rv * idg, rv, acc[1]);
+        const int nt = DIM * nh1;
+        for (int k0 = gtid; k0 < nt; k0 += 2 * gstride) {
+          double idg[2], pv[2], xv[2], qv[2], rv[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = k0 + h * gstride < nt ? k0 + h * gstride : k0;
+            idg[h] = __ldg(a.invdiag + k);
+            pv[h] = a.p[k];
+            xv[h] = a.x[k];
+            qv[h] = a.ap[k];
+            rv[h] = a.r[k];
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = k0 + h * gstride;
+            if (k < nt && idg[h] != 0.0) {
+              a.x[k] = fma(alpha, pv[h], xv[h]);
+              const double r2 = fma(-alpha, qv[h], rv[h]);
+              a.r[k] = r2;
+              acc[0] = fma(r2, r2, acc[0]);
+              acc[1] = fma(r2 * idg[h], r2, acc[1]);
+            }
           }
         }
         bsum<2>(acc, red);
@@ -1134,19 +1163,34 @@ struct Family {
         const bool swept = inner_sweep(beta);
         if (!swept || !sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
         {  // q = M p_new gathered, p = p_new, p.q
+          // (all loads of a node issued before any use: the sweep is latency-bound)
           float acc[5] = {0, 0, 0, 0, 0};
           for (int g = gtid; g < nh1; g += gstride) {
-            int off[1 << DIM];
+            int off[1 << DIM] = {};
             const int n = node_copies<DIM, D>(m, g, DIM, off);
+            float idg[DIM], pv[DIM], rv[DIM], ev[DIM][1 << DIM];
+#pragma unroll
             for (int c = 0; c < DIM; ++c) {
               const int k = c * nh1 + g;
-              const float idg = a.invdiag32[k];
-              float qv = 0.0f, pn = 0.0f;
-              if (idg != 0.0f) {
-                qv = a.evec32[off[0] + c * ND];
-                for (int j = 1; j < n; ++j) qv += a.evec32[off[j] + c * ND];
-                pn = fmaf(beta, a.p32[k], idg * a.r32[k]);
+              idg[c] = __ldg(a.invdiag32 + k);
+              pv[c] = a.p32[k];
+              rv[c] = a.r32[k];
+#pragma unroll
+              for (int j = 0; j < (1 << DIM); ++j) ev[c][j] = j < n ? a.evec32[off[j] + c * ND] : 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+              const int k = c * nh1 + g;
+              float qv = ev[c][0];
+#pragma unroll
+              for (int j = 1; j < (1 << DIM); ++j)
+                if (j < n) qv += ev[c][j];
+              float pn = 0.0f;
+              if (idg[c] != 0.0f) {
+                pn = fmaf(beta, pv[c], idg[c] * rv[c]);
                 acc[0] = fmaf(pn, qv, acc[0]);
+              } else {
+                qv = 0.0f;
               }
               a.ap32[k] = qv;
               a.p32[k] = pn;
@@ -1164,16 +1208,30 @@ struct Family {
         }
         __syncthreads();
         const float alpha = s_f[2];
-        {  // d += alpha p, r -= alpha q, r.r, r.z
+        {  // d += alpha p, r -= alpha q, r.r, r.z (four DOFs per step, loads first)
           float acc[5] = {0, 0, 0, 0, 0};
-          for (int k = gtid; k < DIM * nh1; k += gstride) {
-            const float idg = a.invdiag32[k];
-            if (idg != 0.0f) {
-              a.d32[k] = fmaf(alpha, a.p32[k], a.d32[k]);
-              const float rv = fmaf(-alpha, a.ap32[k], a.r32[k]);
-              a.r32[k] = rv;
-              acc[0] = fmaf(rv, rv, acc[0]);
-              acc[1] = fmaf(rv * idg, rv, acc[1]);
+          const int nt = DIM * nh1;
+          for (int k0 = gtid; k0 < nt; k0 += 4 * gstride) {
+            float idg[4], pv[4], dv[4], qv[4], rv[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int k = k0 + h * gstride < nt ? k0 + h * gstride : k0;
+              idg[h] = __ldg(a.invdiag32 + k);
+              pv[h] = a.p32[k];
+              dv[h] = a.d32[k];
+              qv[h] = a.ap32[k];
+              rv[h] = a.r32[k];
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int k = k0 + h * gstride;
+              if (k < nt && idg[h] != 0.0f) {
+                a.d32[k] = fmaf(alpha, pv[h], dv[h]);
+                const float r2 = fmaf(-alpha, qv[h], rv[h]);
+                a.r32[k] = r2;
+                acc[0] = fmaf(r2, r2, acc[0]);
+                acc[1] = fmaf(r2 * idg[h], r2, acc[1]);
+              }
             }
           }
           block_sum_f(acc);

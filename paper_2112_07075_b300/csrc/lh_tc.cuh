@@ -85,7 +85,7 @@ struct TcMass {
 
   char *img, *areg, *mqs;
   uint64_t *bars;   // [0] MMA completion, [1] [2] q-chunk buffers, [3] bulk copies (image, mq tile)
-  int *s_base;      // per tile row: component offset + the element's base H1 node (-1: padding row)
+  int *s_base;      // per element of the tile: its base H1 node
   uint32_t tmem;
   uint32_t n_mma, n_buf[2], n_copy;   // phases completed so far (the same in every thread)
 
@@ -160,29 +160,68 @@ struct TcMass {
         tc::mbar_arrive_expect_tx(&bars[3], bytes);
         tc::bulk_g2s(mqs, a.mq32 + (size_t)e_lo * NQ, bytes, &bars[3]);
       }
-      if (threadIdx.x < L::ROWS) {
-        const int R = R0 + threadIdx.x;
-        s_base[threadIdx.x] = R < rows_total ? (R % 3) * m.nh1 + h1_base<3, D>(m, R / 3) : -1;
+      const int ne_t = e_hi - e_lo + 1;   // elements of this tile (the first and last may be partial)
+      if (threadIdx.x < ne_t) s_base[threadIdx.x] = h1_base<3, D>(m, e_lo + threadIdx.x);
+      if (L::NKB * 64 > ND || R0 + L::ROWS > rows_total) {   // padding columns / rows must read as 0
+        for (int k = threadIdx.x; k < L::A1 / 16; k += THREADS)
+          reinterpret_cast<uint4 *>(areg)[k] = make_uint4(0u, 0u, 0u, 0u);
       }
       __syncthreads();
-      // X: p_new at the rows' element nodes, split hi/lo, K-major swizzled blocks
-      for (int u = threadIdx.x; u < L::ROWS * L::NKB * 8; u += THREADS) {
-        const int r = u % L::ROWS, j = u / L::ROWS;   // row, 8-node chunk
-        const int base = s_base[r];
-        float v[8];
+      // X = u at the tile's element nodes, gathered along mesh lines: a warp takes
+      // one (component, iy, iz) line and its lanes walk the tile's elements and
+      // their x-nodes, i.e. consecutive H1 nodes (one repeat per element face), so
+      // the loads are coalesced; values go to the swizzled hi/lo blocks.
+      {
+        const int seg = ne_t * D;   // (element, ix) pairs of one line
+        for (int line = warp; line < 3 * D * D; line += THREADS / 32) {
+          const int c = line / (D * D), iy = line % D, iz = (line / D) % D;
+          const int r_c = 3 * e_lo + c - R0;   // row of (e_lo, c); rows step by 3 per element
+          const int goff = c * m.nh1 + m.n1x * (iy + m.n1y * iz);
+          const int i_line = D * (iy + D * iz);
+          constexpr int J = (L::MQ_E * D + 31) / 32;
+          // every load is issued unconditionally (at a valid index) so that all of
+          // a lane's loads are in flight together; invalid slots are zeroed after
+          float v[J];
+          {
+            float ld0[J], ld1[J], ld2[J];
 #pragma unroll
-        for (int l = 0; l < 8; ++l) {
-          const int i = j * 8 + l;
-          v[l] = (base >= 0 && i < ND)
-                     ? F::template dir_value<MODE, float>(base + h1_local<3, D>(m, i), a.invdiag32, a.d32, a.r32,
-                                                       a.ap32, a.p32, 0.0f, beta)
-                     : 0.0f;
+            for (int jj = 0; jj < J; ++jj) {
+              const int k = lane + 32 * jj;
+              const int el = k < seg ? k / D : 0, ix = k < seg ? k - (k / D) * D : 0;
+              const int gi = goff + s_base[el] + ix;
+              ld0[jj] = __ldg(a.invdiag32 + gi);
+              if constexpr (MODE == 0) {
+                ld1[jj] = a.d32[gi];
+              } else {
+                ld1[jj] = a.r32[gi];
+                ld2[jj] = a.p32[gi];
+              }
+            }
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) {
+              const int k = lane + 32 * jj;
+              const int r = r_c + 3 * (k / D);
+              float val;
+              if constexpr (MODE == 0) val = ld0[jj] != 0.0f ? ld1[jj] : 0.0f;   // masked x
+              else val = fmaf(beta, ld2[jj], ld0[jj] * ld1[jj]);                  // invdiag r + beta p
+              v[jj] = (k < seg && r >= 0 && r < L::ROWS) ? val : 0.0f;
+            }
+          }
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) {
+            const int k = lane + 32 * jj;
+            const int el = k / D, ix = k - el * D;
+            const int r = r_c + 3 * el;
+            if (k < seg && r >= 0 && r < L::ROWS) {
+              const int i = i_line + ix;
+              const __nv_bfloat16 h = __float2bfloat16_rn(v[jj]);
+              const __nv_bfloat16 l = __float2bfloat16_rn(v[jj] - __bfloat162float(h));
+              const int off = (i >> 6) * L::A_BLOCK + L::sw128(r, i & 63);
+              *reinterpret_cast<__nv_bfloat16 *>(areg + off) = h;
+              *reinterpret_cast<__nv_bfloat16 *>(areg + L::NKB * L::A_BLOCK + off) = l;
+            }
+          }
         }
-        uint4 hi, lo;
-        tc::split8(v, hi, lo);
-        const int off = (j >> 3) * L::A_BLOCK + L::sw128(r, (j & 7) * 8);
-        *reinterpret_cast<uint4 *>(areg + off) = hi;
-        *reinterpret_cast<uint4 *>(areg + L::NKB * L::A_BLOCK + off) = lo;
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
