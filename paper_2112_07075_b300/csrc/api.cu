@@ -293,7 +293,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {&c->evec, NE * dim * c->nd},    {&c->r, NV},                 {&c->pv, NV},
       {&c->ap, NV},                    {&c->a_prev, NV},            {&c->rhs, NV},
       {&c->xh, NV},                    {&c->vh, NV},                {&c->vb, NV},
-      {&c->eh, NE * c->nl},            {&c->partials, npart},
+      {&c->eh, NE * c->nl},            {&c->partials, npart},         {&c->zv, NV},
       {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
       {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
       {(double **)&c->ap32, nf * (NV + 1) / 2},       {(double **)&c->d32, nf * (NV + 1) / 2},
@@ -561,6 +561,7 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
   a.r = c->r;
   a.p = c->pv;
   a.ap = c->ap;
+  a.z = c->zv;
   a.evec = c->evec;
   a.partials = c->partials;
   a.bar = c->bar;

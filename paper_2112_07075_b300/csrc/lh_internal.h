@@ -68,6 +68,7 @@ struct CgArgs {
   MeshDesc mesh;
   const double *tab, *mq, *invdiag, *b;
   double *x, *r, *p, *ap, *evec, *partials;
+  double *z;                 // invdiag * r, kept with r
   void *bar;                 // GridBarrier
   int *status;
   lh_cg_info *info;
@@ -188,7 +189,7 @@ struct lh_ctx {
   double *tab = nullptr, *verts = nullptr, *x0 = nullptr, *rho0 = nullptr, *mq = nullptr, *jinv0 = nullptr,
          *D = nullptr, *me_inv = nullptr, *invdiag = nullptr, *evec = nullptr, *r = nullptr, *pv = nullptr,
          *ap = nullptr, *a_prev = nullptr, *rhs = nullptr, *xh = nullptr, *vh = nullptr, *vb = nullptr,
-         *eh = nullptr, *partials = nullptr;
+         *eh = nullptr, *partials = nullptr, *zv = nullptr;
   float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
         *evec32 = nullptr;
   int grid_cg_ir = 0, grid_cg_tc = 0;

@@ -657,7 +657,8 @@ struct Family {
   }
 
   // Search-direction value at a node: p_new = invdiag*(r - alpha q) + beta p (MODE 2),
-  // p0 = invdiag*r (MODE 1), invdiag*r + beta p (MODE 3), or the masked vector x (MODE 0).
+  // p0 = invdiag*r (MODE 1), invdiag*r + beta p (MODE 3), z + beta p with z = invdiag*r
+  // passed as x (MODE 4), or the masked vector x (MODE 0).
   template <int MODE, typename T>
   static __device__ __forceinline__ T dir_value(int gi, const T *__restrict__ idv, const T *x, const T *r,
                                                 const T *q, const T *p, T alpha, T beta) {
@@ -665,6 +666,7 @@ struct Family {
     if (MODE == 0) return idg != (T)0 ? x[gi] : (T)0;
     if (MODE == 1) return idg * r[gi];
     if (MODE == 3) return fma(beta, p[gi], idg * r[gi]);
+    if (MODE == 4) return fma(beta, p[gi], x[gi]);   // x holds z = invdiag r
     return fma(beta, p[gi], idg * fma(-alpha, q[gi], r[gi]));
   }
 
@@ -759,45 +761,6 @@ struct Family {
     }
   }
 
-  // Node sweep that closes iteration k and opens k+1 (MODE 2), or starts the
-  // solve (MODE 1: p = invdiag r): r' = r - alpha q, x' = x + alpha p,
-  // p' = invdiag r' + beta p, q' = gathered E-vector; accumulates
-  // (p',q'), (r',z'), (q',z'), (q', invdiag q'), (r',r') into acc[0..4].
-  template <int MODE, typename T>
-  static __device__ __forceinline__ void sweep_nodes(const MeshDesc &m, const T *__restrict__ idv, T *x, T *r, T *q,
-                                                     T *p, const T *evec, T alpha, T beta, T (&acc)[5]) {
-    const int nh1 = m.nh1;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nh1; g += gridDim.x * blockDim.x) {
-      int off[1 << DIM];
-      const int n = node_copies<DIM, D>(m, g, DIM, off);
-      for (int c = 0; c < DIM; ++c) {
-        const int k = c * nh1 + g;
-        const T idg = idv[k];
-        if (idg == (T)0) continue;   // constrained DOF: r, p, q stay 0
-        T rv = r[k], pv = (T)0;
-        if (MODE == 2) {
-          const T pk = p[k];
-          rv = fma(-alpha, q[k], rv);
-          x[k] = fma(alpha, pk, x[k]);
-          pv = fma(beta, pk, idg * rv);
-          r[k] = rv;
-        } else {
-          pv = idg * rv;
-        }
-        T qv = evec[off[0] + c * ND];
-        for (int j = 1; j < n; ++j) qv += evec[off[j] + c * ND];
-        p[k] = pv;
-        q[k] = qv;
-        const T z = idg * rv;
-        acc[0] = fma(pv, qv, acc[0]);
-        acc[1] = fma(rv, z, acc[1]);
-        acc[2] = fma(qv, z, acc[2]);
-        acc[3] = fma(qv * idg, qv, acc[3]);
-        acc[4] = fma(rv, rv, acc[4]);
-      }
-    }
-  }
-
   static constexpr size_t cg_smem() { return sizeof(double) * (TAB + CXC * ND + MC_S + CXC * NQ + CXC * ND + RED); }
   // Standard Jacobi PCG, three grid barriers per iteration. (A one-reduction
   // variant with a scalar recurrence for beta saves a barrier but costs ~5 %
@@ -858,6 +821,7 @@ struct Family {
             a.x[k] = 0.0;
           }
           a.r[k] = rv;
+          a.z[k] = rv * idg;
           a.p[k] = 0.0;
           a.ap[k] = 0.0;
         }
@@ -889,8 +853,8 @@ struct Family {
       __syncthreads();
       const double beta = s_sc[5];
       rz_old = rz;
-      // E-vector of M p_new, p_new = invdiag r + beta p
-      sweep_matvec<3, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.x, a.r, a.ap, a.p, 0.0, beta,
+      // E-vector of M p_new, p_new = z + beta p (z = invdiag r, stored by the r update)
+      sweep_matvec<4, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.z, a.r, a.ap, a.p, 0.0, beta,
                               a.evec);
       if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
       {  // q = M p_new, p = p_new, p.q (all loads of a node before any use)
@@ -898,13 +862,13 @@ struct Family {
         for (int g = gtid; g < nh1; g += gstride) {
           int off[1 << DIM] = {};
           const int n = node_copies<DIM, D>(m, g, DIM, off);
-          double idg[DIM], pv[DIM], rv[DIM];
+          double idg[DIM], pv[DIM], zv[DIM];
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {
             const int k = c * nh1 + g;
             idg[c] = __ldg(a.invdiag + k);
             pv[c] = a.p[k];
-            rv[c] = a.r[k];
+            zv[c] = a.z[k];
           }
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {   // one component's copies at a time (register budget)
@@ -918,7 +882,7 @@ struct Family {
               if (j < n) qv += ev[j];
             double pn = 0.0;
             if (idg[c] != 0.0) {
-              pn = fma(beta, pv[c], idg[c] * rv[c]);
+              pn = fma(beta, pv[c], zv[c]);
               acc[0] = fma(pn, qv, acc[0]);
             } else {
               qv = 0.0;
@@ -957,9 +921,11 @@ struct Family {
             if (k < nt && idg[h] != 0.0) {
               a.x[k] = fma(alpha, pv[h], xv[h]);
               const double r2 = fma(-alpha, qv[h], rv[h]);
+              const double z2 = r2 * idg[h];
               a.r[k] = r2;
+              a.z[k] = z2;
               acc[0] = fma(r2, r2, acc[0]);
-              acc[1] = fma(r2 * idg[h], r2, acc[1]);
+              acc[1] = fma(z2, r2, acc[1]);
             }
           }
         }
