@@ -175,18 +175,19 @@ __device__ __forceinline__ double eig_min2(double a, double b, double c, double 
 // from the largest cross product of two rows of (A - lam I).
 __device__ __forceinline__ double eig_min3(const double *A, double *s) {
   const double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[4], a12 = A[5], a22 = A[8];
-  const double q = (a00 + a11 + a22) / 3.0;
+  constexpr double third = 1.0 / 3.0, sixth = 1.0 / 6.0;
+  const double q = (a00 + a11 + a22) * third;
   const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
   const double d0 = a00 - q, d1 = a11 - q, d2 = a22 - q;
   const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
-  const double pp = sqrt(p2 / 6.0);
+  const double pp = sqrt(p2 * sixth);
   double lam = q;
   if (pp > 0.0) {
     const double ip = 1.0 / pp;
     const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
     const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
     const double r = fmin(fmax(0.5 * detb, -1.0), 1.0);
-    const double phi = acos(r) / 3.0;
+    const double phi = acos(r) * third;
     lam = q + 2.0 * pp * cos(phi + 2.0943951023931957);  // 2*pi/3
   }
   if (s) {
@@ -196,16 +197,18 @@ __device__ __forceinline__ double eig_min3(const double *A, double *s) {
     const double *ra[3] = {r0, r0, r1}, *rb[3] = {r1, r2, r2};
     double nbest = -1.0;
     int kbest = 0;
+    // candidates compared by squared norm; one square root for the chosen one
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       cr[k][0] = ra[k][1] * rb[k][2] - ra[k][2] * rb[k][1];
       cr[k][1] = ra[k][2] * rb[k][0] - ra[k][0] * rb[k][2];
       cr[k][2] = ra[k][0] * rb[k][1] - ra[k][1] * rb[k][0];
-      const double n = sqrt(cr[k][0] * cr[k][0] + cr[k][1] * cr[k][1] + cr[k][2] * cr[k][2]);
-      if (n > nbest) { nbest = n; kbest = k; }
+      const double n2 = cr[k][0] * cr[k][0] + cr[k][1] * cr[k][1] + cr[k][2] * cr[k][2];
+      if (n2 > nbest) { nbest = n2; kbest = k; }
     }
     const double nM2 = m00 * m00 + m11 * m11 + m22 * m22 + 2.0 * (a01 * a01 + a02 * a02 + a12 * a12);
-    if (nbest <= kDegen * nM2) {
+    const double dthr = kDegen * nM2;
+    if (nbest <= dthr * dthr) {
       const double nM = sqrt(nM2);
       const double nA = sqrt(a00 * a00 + a11 * a11 + a22 * a22 + 2.0 * p1);
       if (nM <= kDegen * nA || nM == 0.0) {
@@ -232,9 +235,10 @@ __device__ __forceinline__ double eig_min3(const double *A, double *s) {
         s[0] = c0 / n; s[1] = c1 / n; s[2] = c2 / n;
       }
     } else {
-      s[0] = cr[kbest][0] / nbest;
-      s[1] = cr[kbest][1] / nbest;
-      s[2] = cr[kbest][2] / nbest;
+      const double inv = 1.0 / sqrt(nbest);
+      s[0] = cr[kbest][0] * inv;
+      s[1] = cr[kbest][1] * inv;
+      s[2] = cr[kbest][2] * inv;
     }
   }
   return lam;
@@ -253,23 +257,23 @@ __device__ __forceinline__ QPointOut qpoint_physics(const double *J, const doubl
                                                     bool want_dt, double *Dout) {
   QPointOut o;
   double Ji[DIM * DIM];
-  double det;
+  double det, id;
   if constexpr (DIM == 2) {
     det = J[0] * J[3] - J[1] * J[2];
-    const double id = 1.0 / det;
+    id = 1.0 / det;
     Ji[0] = J[3] * id; Ji[1] = -J[1] * id; Ji[2] = -J[2] * id; Ji[3] = J[0] * id;
   } else {
     const double c00 = J[4] * J[8] - J[5] * J[7];
     const double c01 = J[5] * J[6] - J[3] * J[8];
     const double c02 = J[3] * J[7] - J[4] * J[6];
     det = J[0] * c00 + J[1] * c01 + J[2] * c02;
-    const double id = 1.0 / det;
+    id = 1.0 / det;
     Ji[0] = c00 * id; Ji[1] = (J[2] * J[7] - J[1] * J[8]) * id; Ji[2] = (J[1] * J[5] - J[2] * J[4]) * id;
     Ji[3] = c01 * id; Ji[4] = (J[0] * J[8] - J[2] * J[6]) * id; Ji[5] = (J[2] * J[3] - J[0] * J[5]) * id;
     Ji[6] = c02 * id; Ji[7] = (J[1] * J[6] - J[0] * J[7]) * id; Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
   }
   o.inverted = !(det > 0.0);
-  const double rho = m * iw / det;
+  const double rho = m * iw * id;
   const double ep = fmax(e_q, 0.0);
   const double pres = (pp.gamma - 1.0) * rho * ep;
   const double cs = sqrt(pp.gamma * (pp.gamma - 1.0) * ep);
@@ -284,11 +288,15 @@ __device__ __forceinline__ QPointOut qpoint_physics(const double *J, const doubl
       for (int l = 1; l < DIM; ++l) s = fma(dV[c * DIM + l], Ji[l * DIM + b], s);
       gv[c * DIM + b] = s;
     }
-  double eps[DIM * DIM];
+  double eps[DIM * DIM];   // symmetric: the upper triangle is computed and mirrored
 #pragma unroll
   for (int c = 0; c < DIM; ++c)
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) eps[c * DIM + b] = 0.5 * (gv[c * DIM + b] + gv[b * DIM + c]);
+    for (int b = c; b < DIM; ++b) {
+      const double v = 0.5 * (gv[c * DIM + b] + gv[b * DIM + c]);
+      eps[c * DIM + b] = v;
+      eps[b * DIM + c] = v;
+    }
   double sigma[DIM * DIM];
 #pragma unroll
   for (int k = 0; k < DIM * DIM; ++k) sigma[k] = 0.0;
@@ -345,11 +353,17 @@ __device__ __forceinline__ QPointOut qpoint_physics(const double *J, const doubl
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) JtJ[c * 3 + b] = J[c] * J[b] + J[3 + c] * J[3 + b] + J[6 + c] * J[6 + b];
+        for (int b = c; b < 3; ++b) {
+          const double v = J[c] * J[b] + J[3 + c] * J[3 + b] + J[6 + c] * J[6 + b];
+          JtJ[c * 3 + b] = v;
+          JtJ[b * 3 + c] = v;
+        }
       lamJ = eig_min3(JtJ, nullptr);
     }
-    const double hmin = sqrt(fmax(lamJ, 0.0)) / pp.order;
-    o.inv_dt = cs / hmin + 2.5 * mu / (rho * hmin * hmin);
+    // h_min = sqrt(lamJ) / p; 1/dt = c_s / h_min + 2.5 mu / (rho h_min^2), one division
+    const double l2 = fmax(lamJ, 0.0);
+    const double hm = sqrt(l2);   // p h_min
+    o.inv_dt = pp.order * (cs * rho * hm + 2.5 * pp.order * mu) / (rho * l2);
     if (o.inverted) o.inv_dt = INFINITY;
   }
   return o;
