@@ -312,6 +312,9 @@ lh_status lh_mlp_gradients(lh_mlp *m, const float *X, const float *T, int n, flo
 lh_status lh_mlp_train_step(lh_mlp *m, const float *X, const float *T, int n, float lr, float *loss,
                             lh_stream_t stream);
 const char *lh_mlp_last_error(const lh_mlp *m);
+/* Waits for the device, then returns LH_ERR_TIMEOUT (and clears it) if a GEMM of
+ * this MLP gave up a bounded wait since the last call, else LH_OK. */
+lh_status lh_mlp_sync_status(lh_mlp *m);
 
 /* Attach the learned form to a context (3D, order 3, q1 = 6). mode 1: record a
  * training example per element at every mass solve of lh_rk2avg_step that has

@@ -1,6 +1,7 @@
 // Per-element MLP of the learned form: 586 -> 128 -> 128 -> 192, GELU (erf form)
 // after both hidden layers, BF16 weights and activations on the tensor cores
-// (mma.sync m16n8k16, FP32 accumulation), FP32 master weights, Adam.
+// (tcgen05 MMA fed by TMA, FP32 accumulation in tensor memory), FP32 master
+// weights, Adam.
 // Used to predict the mass-CG initial guess (see learned.cu); this file holds
 // the network itself: parameter init, forward, backward, optimiser step.
 #include <cuda_bf16.h>
@@ -11,24 +12,34 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "lh_device.cuh"
 #include "lh_internal.h"
 #include "lh_mlp.h"
+#include "tc_sm100.cuh"
 
 namespace lh {
 namespace mlp {
 namespace {
 
 // ---------------------------------------------------------------------------
-// BF16 GEMM on the tensor cores: C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]),
-// FP32 accumulation. A is row-major (A[m*lda+k]) or column-major (A[k*lda+m]);
-// B is "n-major" (B[n*ldb+k], i.e. a row-major weight matrix used as B = W^T)
-// or row-major (B[k*ldb+n]). Block tile 64x64x32, 4 warps (2x2), each warp 32x32
-// with m16n8k16 MMAs. Out-of-range rows/cols/k read as zero.
-// Epilogue: C32 (FP32) and/or C16 (BF16) with optional bias and GELU; when
-// PRE is given the pre-activation is written there (FP32).
+// BF16 GEMM on the 5th-generation tensor cores: C[m][n] = sum_k A(m,k) B(k,n)
+// (+ bias[n]), FP32 accumulation in tensor memory. A is K-major (A[m*lda+k]) or
+// MN-major (A[k*lda+m]); B is K-major (B[n*ldb+k], a row-major weight used as
+// B = W^T) or MN-major (B[k*ldb+n]). A CTA owns a 128 x BN tile: one thread
+// issues TMA tile loads (cp.async.bulk.tensor, 128-byte swizzle, zero fill past
+// the extents) into a 4-stage ring, one thread issues tcgen05.mma (K = 16 per
+// instruction) and releases stages by tcgen05.commit; the four warps then read
+// the accumulator rows back with tcgen05.ld for the epilogue. With splits > 1
+// the K range is cut into `splits` slices (grid z) whose FP32 partial tiles are
+// summed afterwards in a fixed order (k_split_sum): deterministic.
+// Epilogue: C32 (FP32) and/or C16 (BF16) with optional bias and GELU; when PRE
+// is given the pre-activation is written there (FP32).
 // ---------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8;
+constexpr int kStages = 4;
+constexpr int kBK = 64;   // K per stage: one 128-byte swizzle row of BF16
+constexpr long long kSpin = 2000000000LL;   // bounded waits (~1 s)
 
 enum { A_ROW = 0, A_COL = 1 };
 enum { B_NMAJOR = 0, B_ROW = 1 };
@@ -41,6 +52,18 @@ struct GemmArgs {
   __nv_bfloat16 *C16;
   float *pre;
   int ldc, gelu, accumulate;
+  int splits;       // K slices (grid z); > 1 writes partial tiles
+  float *partial;   // [splits][M][N] FP32 when splits > 1
+  int *status;      // LH_ERR_TIMEOUT latched here if a bounded wait gives up
+};
+
+template <int BN>
+struct GemmCfg {
+  static constexpr int A_BYTES = 128 * kBK * 2;
+  static constexpr int B_BYTES = BN * kBK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int SMEM = 1024 + kStages * STAGE;
+  static constexpr int TCOLS = BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -48,95 +71,201 @@ __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+// TMA: 2D tile (x = inner coordinate, y = outer) into shared memory, counted on bar.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(tc::smem_u32(bar))
+      : "memory");
 }
 
-template <int AL, int BL>
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 sA[BM][PADK];   // [m][k]
-  __shared__ __align__(16) __nv_bfloat16 sB[BN][PADK];   // [n][k]
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int grp = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int t = threadIdx.x; t < BM * BK; t += 128) {
-      int mm, kk;
-      if (AL == A_ROW) { mm = t / BK; kk = t % BK; } else { kk = t / BM; mm = t % BM; }
-      const int m = m0 + mm, k = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (m < g.M && k < g.K) v = AL == A_ROW ? g.A[(size_t)m * g.lda + k] : g.A[(size_t)k * g.lda + m];
-      sA[mm][kk] = v;
+// Instruction descriptor of kind::f16, BF16 inputs, FP32 accumulator, with the
+// A and B major-ness bits (15: A MN-major, 16: B MN-major).
+__host__ __device__ constexpr uint32_t idesc_ab(int M, int N, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int AL, int BL, int BN>
+__global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                 const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+  using C = GemmCfg<BN>;
+  extern __shared__ unsigned char gemm_smem_raw[];
+  char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * BN;
+  const int kblocks = (g.K + kBK - 1) / kBK;
+  const int per = (kblocks + g.splits - 1) / g.splits;
+  const int kb0 = blockIdx.z * per;
+  const int nkb = max(0, min(kblocks, kb0 + per) - kb0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
     }
-    for (int t = threadIdx.x; t < BN * BK; t += 128) {
-      int nn, kk;
-      if (BL == B_NMAJOR) { nn = t / BK; kk = t % BK; } else { kk = t / BN; nn = t % BN; }
-      const int n = n0 + nn, k = k0 + kk;
-      __nv_bfloat16 v = zero;
-      if (n < g.N && k < g.K) v = BL == B_NMAJOR ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
-      sB[nn][kk] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      unsigned af[2][4], bf[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + grp;
-        af[i][0] = *(const unsigned *)&sA[r][ks + tig * 2];
-        af[i][1] = *(const unsigned *)&sA[r + 8][ks + tig * 2];
-        af[i][2] = *(const unsigned *)&sA[r][ks + tig * 2 + 8];
-        af[i][3] = *(const unsigned *)&sA[r + 8][ks + tig * 2 + 8];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + grp;
-        bf[j][0] = *(const unsigned *)&sB[c][ks + tig * 2];
-        bf[j][1] = *(const unsigned *)&sB[c][ks + tig * 2 + 8];
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
-    }
-    __syncthreads();
+    tc::mbar_init(&done, 1);
+    tc::fence_mbar_init();
+    s_fail = 0;
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + grp + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
-        if (m >= g.M || n >= g.N) continue;
-        float z = acc[i][j][r];
-        if (g.bias) z += g.bias[n];
-        const size_t idx = (size_t)m * g.ldc + n;
-        if (g.pre) g.pre[idx] = z;
-        const float o = g.gelu ? gelu_f(z) : z;
-        if (g.C32) g.C32[idx] = g.accumulate ? g.C32[idx] + o : o;
-        if (g.C16) g.C16[idx] = __float2bfloat16(o);
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(&s_tmem, C::TCOLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  constexpr uint32_t IDESC = idesc_ab(128, BN, AL == A_COL, BL == B_ROW);
+  if (threadIdx.x == 0) {   // producer: TMA tile loads into the ring
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages, u = i / kStages;
+      if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, kSpin)) { s_fail = 1; break; }
+      char *sa = base + s * C::STAGE, *sb = sa + C::A_BYTES;
+      tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
+      const int k0 = (kb0 + i) * kBK;
+      if (AL == A_ROW) {
+        tma_load_2d(sa, &tmA, k0, m0, &full[s]);
+      } else {
+        tma_load_2d(sa, &tmA, m0, k0, &full[s]);
+        tma_load_2d(sa + 8192, &tmA, m0 + 64, k0, &full[s]);
       }
+      if (BL == B_NMAJOR) {
+        tma_load_2d(sb, &tmB, k0, n0, &full[s]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < BN / 64; ++j) tma_load_2d(sb + j * 8192, &tmB, n0 + 64 * j, k0, &full[s]);
+      }
+    }
+  } else if (threadIdx.x == 32) {   // MMA issuer
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages, u = i / kStages;
+      if (!tc::mbar_wait(&full[s], u & 1, kSpin)) { s_fail = 1; break; }
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(base + s * C::STAGE), b0 = a0 + C::A_BYTES;
+#pragma unroll
+      for (int ks = 0; ks < kBK / 16; ++ks) {
+        // K-major: the 16-wide K step moves 32 bytes along the swizzled row;
+        // MN-major: it moves two 8-row atoms (2 KB); 64-wide MN blocks are 8 KB apart
+        const uint64_t ad = AL == A_ROW ? tc::sdesc(a0 + ks * 32, 16, 1024) : tc::sdesc(a0 + ks * 2048, 8192, 1024);
+        const uint64_t bd = BL == B_NMAJOR ? tc::sdesc(b0 + ks * 32, 16, 1024) : tc::sdesc(b0 + ks * 2048, 8192, 1024);
+        tc::mma_bf16(tmem, ad, bd, IDESC, (i > 0 || ks > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(&done);
+  }
+  __syncwarp();
+  const bool ok = nkb == 0 || tc::mbar_wait(&done, 0, kSpin);
+  const int all_ok = __syncthreads_and(ok ? 1 : 0) && !s_fail;
+  if (!all_ok && threadIdx.x == 0 && g.status) atomicExch(g.status, 6);
+  tc::fence_after_sync();
+  if (all_ok) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = m0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      if (nkb > 0) {
+        tc::tmem_ld16(tl + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int l = 0; l < 16; ++l) v[l] = 0.0f;
+      }
+      const int n = n0 + c0;   // N is a multiple of 16: a chunk is all in or all out
+      if (m >= g.M || n >= g.N) continue;
+      if (g.splits > 1) {
+        float *dst = g.partial + ((size_t)blockIdx.z * g.M + m) * g.N + n;
+#pragma unroll
+        for (int l = 0; l < 16; l += 4) *reinterpret_cast<float4 *>(dst + l) = make_float4(v[l], v[l + 1], v[l + 2], v[l + 3]);
+        continue;
+      }
+      const size_t idx = (size_t)m * g.ldc + n;
+#pragma unroll
+      for (int l = 0; l < 16; ++l) {
+        float z = v[l];
+        if (g.bias) z += g.bias[n + l];
+        if (g.pre) g.pre[idx + l] = z;
+        const float o = g.gelu ? gelu_f(z) : z;
+        if (g.C32) g.C32[idx + l] = g.accumulate ? g.C32[idx + l] + o : o;
+        if (g.C16) g.C16[idx + l] = __float2bfloat16(o);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, C::TCOLS);
 }
 
-template <int AL, int BL>
-void gemm(const GemmArgs &g, cudaStream_t s) {
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  k_gemm<AL, BL><<<grid, 128, 0, s>>>(g);
+// C32[m][n] (+)= sum over slices of partial[z][m][n], slices in order.
+__global__ void k_split_sum(int splits, int M, int N, const float *__restrict__ partial, float *__restrict__ C,
+                            int ldc, int accumulate) {
+  const size_t total = (size_t)M * N;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += partial[(size_t)z * total + t];
+    const size_t idx = (t / N) * (size_t)ldc + t % N;
+    C[idx] = accumulate ? C[idx] + s : s;
+  }
+}
+
+// Host: 2D BF16 tensor map (inner x outer elements, row pitch in bytes) with
+// the 128-byte swizzle and a box of box_inner x box_outer.
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+bool make_tmap(CUtensorMap *tm, const void *ptr, int inner, int outer, int pitch_elems, int box_inner, int box_outer) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launch C = A B with the layouts AL/BL (see k_gemm); returns false if a tensor
+// map cannot be built or the launch fails.
+template <int AL, int BL, int BN>
+bool gemm(GemmArgs g, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  // A(m,k): K-major = [M rows][K cols]; MN-major = [K rows][M cols]
+  const bool okA = AL == A_ROW ? make_tmap(&ta, g.A, g.K, g.M, g.lda, kBK, 128)
+                               : make_tmap(&ta, g.A, g.M, g.K, g.lda, 64, kBK);
+  // B(k,n): K-major = [N rows][K cols]; MN-major = [K rows][N cols]
+  const bool okB = BL == B_NMAJOR ? make_tmap(&tb, g.B, g.K, g.N, g.ldb, kBK, BN)
+                                  : make_tmap(&tb, g.B, g.N, g.K, g.ldb, 64, kBK);
+  if (!okA || !okB) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute((const void *)k_gemm<AL, BL, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         GemmCfg<BN>::SMEM);
+    attr = true;
+  }
+  if (g.splits < 1) g.splits = 1;
+  dim3 grid((g.N + BN - 1) / BN, (g.M + 127) / 128, g.splits);
+  k_gemm<AL, BL, BN><<<grid, 128, GemmCfg<BN>::SMEM, s>>>(ta, tb, g);
+  if (g.splits > 1)
+    k_split_sum<<<296, 256, 0, s>>>(g.splits, g.M, g.N, g.partial, g.C32, g.ldc, g.accumulate);
+  return cudaGetLastError() == cudaSuccess;
 }
 
 // --- elementwise helpers -----------------------------------------------------
@@ -254,6 +383,8 @@ struct lh_mlp {
   // activations for up to max_rows rows
   __nv_bfloat16 *Xh = nullptr, *H1h = nullptr, *H2h = nullptr, *dY = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
   float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dH2 = nullptr, *dH1 = nullptr, *part = nullptr;
+  float *split = nullptr;   // split-K partial tiles of the weight-gradient GEMMs
+  int *status = nullptr;    // LH_ERR_TIMEOUT latched by a GEMM whose bounded wait gave up
   double *lpart = nullptr;
   int steps = 0;
   std::string err;
@@ -261,6 +392,17 @@ struct lh_mlp {
 
 namespace {
 constexpr int kColParts = 64;
+constexpr int kMaxSplits = 32;
+
+// K slices for a weight-gradient GEMM (K = rows): about one CTA per SM in total.
+int splits_for(int M, int N, int BN, int K) {
+  const int tiles = ((N + BN - 1) / BN) * ((M + 127) / 128);
+  const int kb = (K + kBK - 1) / kBK;
+  int sp = 148 / tiles;
+  if (sp > kMaxSplits) sp = kMaxSplits;
+  if (sp > kb) sp = kb;
+  return sp < 1 ? 1 : sp;
+}
 
 lh_status mfail(lh_mlp *m, lh_status s, const std::string &msg) {
   if (m) m->err = msg;
@@ -269,19 +411,21 @@ lh_status mfail(lh_mlp *m, lh_status s, const std::string &msg) {
 }
 
 // forward pass for n rows already packed in m->Xh; Y (FP32) out
-void forward(lh_mlp *m, int n, float *Y, cudaStream_t s) {
+bool forward(lh_mlp *m, int n, float *Y, cudaStream_t s) {
+  bool ok = true;
   GemmArgs g{};
   g.A = m->Xh; g.B = m->wh + oW1; g.M = n; g.N = kHid; g.K = kInPad; g.lda = kInPad; g.ldb = kInPad;
-  g.bias = m->w + oB1; g.C16 = m->H1h; g.pre = m->Z1; g.ldc = kHid; g.gelu = 1;
-  gemm<A_ROW, B_NMAJOR>(g, s);
+  g.bias = m->w + oB1; g.C16 = m->H1h; g.pre = m->Z1; g.ldc = kHid; g.gelu = 1; g.status = m->status;
+  ok = ok && gemm<A_ROW, B_NMAJOR, kHid>(g, s);
   g = GemmArgs{};
   g.A = m->H1h; g.B = m->wh + oW2; g.M = n; g.N = kHid; g.K = kHid; g.lda = kHid; g.ldb = kHid;
-  g.bias = m->w + oB2; g.C16 = m->H2h; g.pre = m->Z2; g.ldc = kHid; g.gelu = 1;
-  gemm<A_ROW, B_NMAJOR>(g, s);
+  g.bias = m->w + oB2; g.C16 = m->H2h; g.pre = m->Z2; g.ldc = kHid; g.gelu = 1; g.status = m->status;
+  ok = ok && gemm<A_ROW, B_NMAJOR, kHid>(g, s);
   g = GemmArgs{};
   g.A = m->H2h; g.B = m->wh + oW3; g.M = n; g.N = kOut; g.K = kHid; g.lda = kHid; g.ldb = kHid;
-  g.bias = m->w + oB3; g.C32 = Y; g.ldc = kOut;
-  gemm<A_ROW, B_NMAJOR>(g, s);
+  g.bias = m->w + oB3; g.C32 = Y; g.ldc = kOut; g.status = m->status;
+  ok = ok && gemm<A_ROW, B_NMAJOR, kOut>(g, s);
+  return ok;
 }
 
 void colsum(lh_mlp *m, int n, int cols, const __nv_bfloat16 *G, float *out, cudaStream_t s) {
@@ -292,40 +436,45 @@ void colsum(lh_mlp *m, int n, int cols, const __nv_bfloat16 *G, float *out, cuda
 }
 
 // loss and gradients of the mean squared error for n rows (Xh packed, T targets)
-void backward(lh_mlp *m, int n, const float *T, float *loss, cudaStream_t s) {
+bool backward(lh_mlp *m, int n, const float *T, float *loss, cudaStream_t s) {
   const int lb = 296;
+  bool ok = true;
   k_loss_grad<<<lb, 256, 0, s>>>(n, m->Y, T, m->dY, m->lpart);
   k_loss_final<<<1, 32, 0, s>>>(lb, m->lpart, (size_t)n * kOut, loss);
   GemmArgs g{};
   // dW3[o][h] = sum_r dY[r][o] H2[r][h]
   g.A = m->dY; g.B = m->H2h; g.M = kOut; g.N = kHid; g.K = n; g.lda = kOut; g.ldb = kHid;
-  g.C32 = m->g + oW3; g.ldc = kHid;
-  gemm<A_COL, B_ROW>(g, s);
+  g.C32 = m->g + oW3; g.ldc = kHid; g.status = m->status;
+  g.splits = splits_for(kOut, kHid, kHid, n); g.partial = m->split;
+  ok = ok && gemm<A_COL, B_ROW, kHid>(g, s);
   colsum(m, n, kOut, m->dY, m->g + oB3, s);
   // dH2[r][h] = sum_o dY[r][o] W3[o][h]
   g = GemmArgs{};
   g.A = m->dY; g.B = m->wh + oW3; g.M = n; g.N = kHid; g.K = kOut; g.lda = kOut; g.ldb = kHid;
-  g.C32 = m->dH2; g.ldc = kHid;
-  gemm<A_ROW, B_ROW>(g, s);
+  g.C32 = m->dH2; g.ldc = kHid; g.status = m->status;
+  ok = ok && gemm<A_ROW, B_ROW, kHid>(g, s);
   k_gelu_back<<<1024, 256, 0, s>>>((size_t)n * kHid, m->dH2, m->Z2, m->dZ2);
   // dW2[h][k] = sum_r dZ2[r][h] H1[r][k]
   g = GemmArgs{};
   g.A = m->dZ2; g.B = m->H1h; g.M = kHid; g.N = kHid; g.K = n; g.lda = kHid; g.ldb = kHid;
-  g.C32 = m->g + oW2; g.ldc = kHid;
-  gemm<A_COL, B_ROW>(g, s);
+  g.C32 = m->g + oW2; g.ldc = kHid; g.status = m->status;
+  g.splits = splits_for(kHid, kHid, kHid, n); g.partial = m->split;
+  ok = ok && gemm<A_COL, B_ROW, kHid>(g, s);
   colsum(m, n, kHid, m->dZ2, m->g + oB2, s);
   // dH1[r][k] = sum_h dZ2[r][h] W2[h][k]
   g = GemmArgs{};
   g.A = m->dZ2; g.B = m->wh + oW2; g.M = n; g.N = kHid; g.K = kHid; g.lda = kHid; g.ldb = kHid;
-  g.C32 = m->dH1; g.ldc = kHid;
-  gemm<A_ROW, B_ROW>(g, s);
+  g.C32 = m->dH1; g.ldc = kHid; g.status = m->status;
+  ok = ok && gemm<A_ROW, B_ROW, kHid>(g, s);
   k_gelu_back<<<1024, 256, 0, s>>>((size_t)n * kHid, m->dH1, m->Z1, m->dZ1);
   // dW1[h][i] = sum_r dZ1[r][h] X[r][i]
   g = GemmArgs{};
   g.A = m->dZ1; g.B = m->Xh; g.M = kHid; g.N = kInPad; g.K = n; g.lda = kHid; g.ldb = kInPad;
-  g.C32 = m->g + oW1; g.ldc = kInPad;
-  gemm<A_COL, B_ROW>(g, s);
+  g.C32 = m->g + oW1; g.ldc = kInPad; g.status = m->status;
+  g.splits = splits_for(kHid, kInPad, kHid, n); g.partial = m->split;
+  ok = ok && gemm<A_COL, B_ROW, kHid>(g, s);
   colsum(m, n, kHid, m->dZ1, m->g + oB1, s);
+  return ok;
 }
 
 void refresh_bf16(lh_mlp *m, cudaStream_t s) { k_to_bf16<<<512, 256, 0, s>>>(kNParam, m->w, m->wh); }
@@ -343,6 +492,19 @@ void lh_mlp_destroy(lh_mlp *m) {
 
 const char *lh_mlp_last_error(const lh_mlp *m) { return m ? m->err.c_str() : "null mlp"; }
 
+lh_status lh_mlp_sync_status(lh_mlp *m) {
+  if (!m) return LH_ERR_ARG;
+  int st = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost) !=
+                                                    cudaSuccess)
+    return mfail(m, LH_ERR_CUDA, "MLP status read failed");
+  if (st != 0) {
+    cudaMemset(m->status, 0, sizeof(int));
+    return mfail(m, LH_ERR_TIMEOUT, "an MLP GEMM gave up a bounded device wait");
+  }
+  return LH_OK;
+}
+
 lh_status lh_mlp_create(unsigned long long seed, int max_rows, lh_mlp **out) {
   if (!out || max_rows < 1) return mfail(nullptr, LH_ERR_ARG, "bad lh_mlp_create arguments");
   *out = nullptr;
@@ -357,7 +519,8 @@ lh_status lh_mlp_create(unsigned long long seed, int max_rows, lh_mlp **out) {
       {(void **)&m->dZ2, R * kHid * 2}, {(void **)&m->dZ1, R * kHid * 2},   {(void **)&m->Z1, R * kHid * 4},
       {(void **)&m->Z2, R * kHid * 4}, {(void **)&m->Y, R * kOut * 4},      {(void **)&m->dH2, R * kHid * 4},
       {(void **)&m->dH1, R * kHid * 4}, {(void **)&m->part, (size_t)kColParts * kInPad * 4},
-      {(void **)&m->lpart, 4096 * 8}};
+      {(void **)&m->lpart, 4096 * 8},   {(void **)&m->split, (size_t)kMaxSplits * kHid * kInPad * 4},
+      {(void **)&m->status, 256}};
   size_t bytes = 0;
   for (auto &it : items) bytes += (it.bytes + 255) / 256 * 256;
   if (cudaMalloc(&m->arena, bytes) != cudaSuccess) {
@@ -402,7 +565,7 @@ lh_status lh_mlp_forward(lh_mlp *m, const float *X, int n, float *Y, lh_stream_t
   if (n > m->max_rows) return mfail(m, LH_ERR_ARG, "more rows than the MLP was created for");
   cudaStream_t s = (cudaStream_t)stream;
   k_pack_input<<<1024, 256, 0, s>>>(n, X, m->Xh);
-  forward(m, n, Y, s);
+  if (!forward(m, n, Y, s)) return mfail(m, LH_ERR_CUDA, "MLP forward: tensor map or launch failed");
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LH_OK : mfail(m, LH_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -413,8 +576,8 @@ lh_status lh_mlp_gradients(lh_mlp *m, const float *X, const float *T, int n, flo
   if (n > m->max_rows) return mfail(m, LH_ERR_ARG, "more rows than the MLP was created for");
   cudaStream_t s = (cudaStream_t)stream;
   k_pack_input<<<1024, 256, 0, s>>>(n, X, m->Xh);
-  forward(m, n, m->Y, s);
-  backward(m, n, T, loss, s);
+  if (!forward(m, n, m->Y, s) || !backward(m, n, T, loss, s))
+    return mfail(m, LH_ERR_CUDA, "MLP gradients: tensor map or launch failed");
   if (grads) cudaMemcpyAsync(grads, m->g, kNParam * 4, cudaMemcpyDeviceToDevice, s);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LH_OK : mfail(m, LH_ERR_CUDA, cudaGetErrorString(e));

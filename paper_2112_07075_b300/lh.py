@@ -28,7 +28,8 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step", "lh_mass_mult_noalloc",
             "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy",
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
-            "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_learn_attach",
+            "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_sync_status",
+            "lh_learn_attach",
             "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc"]
 
 
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mlp_gradients": (I, [P, VP, VP, I, VP, VP, VP]),
         "lh_mlp_train_step": (I, [P, VP, VP, I, ctypes.c_float, VP, VP]),
         "lh_mlp_last_error": (ctypes.c_char_p, [P]),
+        "lh_mlp_sync_status": (I, [P]),
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
         "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
         "lh_timing_enable": (I, [P, I]),
@@ -370,6 +372,10 @@ class MLP:
         self._check(self.lib.lh_mlp_gradients(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grads),
                                               _ptr(self.loss), _stream()))
         return self.loss
+
+    def sync_status(self) -> int:
+        """LH_ERR_TIMEOUT if a GEMM of this MLP gave up a bounded wait (cleared), else 0."""
+        return int(self.lib.lh_mlp_sync_status(self.h))
 
     def train_step(self, X, T, lr):
         self._check(self.lib.lh_mlp_train_step(self.h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),

@@ -29,15 +29,18 @@ def _data(n, seed):
     return X, T
 
 
-def test_forward_and_gradients_match_bf16_reference():
+# 300 rows: two full 128-row tiles and a ragged one, 5 K-slices of the weight
+# gradients; 4173 rows: 33 tiles and split-K over 66 row blocks with a ragged end
+@pytest.mark.parametrize("n", [300, 4173])
+def test_forward_and_gradients_match_bf16_reference(n):
     from paper_2112_07075_b300.lh import MLP
-    net = MLP(seed=5, max_rows=4096)
+    net = MLP(seed=5, max_rows=4200)
     w = net.get_params().astype(np.float64)
     assert np.all(w.reshape(-1)[ref.OFF_W1:ref.OFF_B1].reshape(ref.HID, ref.IN_PAD)[:, ref.IN:] == 0)
-    X, T = _data(300, 11)
+    X, T = _data(n, 11)
     Xg = torch.from_numpy(X.astype(np.float32)).cuda()
     Tg = torch.from_numpy(T.astype(np.float32)).cuda()
-    Y = torch.zeros((300, ref.OUT), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((n, ref.OUT), dtype=torch.float32, device="cuda")
     net.forward(Xg, Y)
     Yr, _ = ref.forward(w, X, bf16=True)
     assert np.linalg.norm(Y.cpu().numpy() - Yr) <= 1e-3 * np.linalg.norm(Yr)
@@ -48,6 +51,7 @@ def test_forward_and_gradients_match_bf16_reference():
     gg = g.cpu().numpy().astype(np.float64)
     for name, (a, b) in {k: (_tensors(gg)[k], v) for k, v in _tensors(gr).items()}.items():
         assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b), name
+    assert net.sync_status() == 0
     net.close()
 
 
