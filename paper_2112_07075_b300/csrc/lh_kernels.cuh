@@ -685,11 +685,13 @@ struct Family {
   }
 
   // One sweep over all element batches: E-vector of M times the MODE vector.
+  // With dot != nullptr each thread also accumulates sum_e u_e . (M_e u_e) over
+  // the values it stores: the energy u^T M u of the swept vector, element by element.
   template <int MODE, typename T>
   static __device__ __forceinline__ void sweep_matvec(const MeshDesc &m, int *eb, const T *tb, const T *tbt, T *u,
                                                       T *S, T *uq, T *y, const T *mq, const T *idv, const T *x,
                                                       const T *r, const T *q, const T *p, T alpha, T beta,
-                                                      T *evec) {
+                                                      T *evec, T *dot = nullptr) {
     const int nbatch = (m.ne + NBC - 1) / NBC;
     for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
       const int e0 = bt * NBC, nb = min(NBC, m.ne - e0);
@@ -703,7 +705,17 @@ struct Family {
       }
       __syncthreads();
       batch_matvec<T>(tb, tbt, u, S, uq, y, mq, e0, nb);
-      for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) evec[(size_t)e0 * DIM * ND + k] = y[k];
+      if (dot) {
+        T d = *dot;
+        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) {
+          const T yk = y[k];
+          evec[(size_t)e0 * DIM * ND + k] = yk;
+          d = fma(u[k], yk, d);
+        }
+        *dot = d;
+      } else {
+        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) evec[(size_t)e0 * DIM * ND + k] = y[k];
+      }
       __syncthreads();
     }
   }
@@ -728,7 +740,7 @@ struct Family {
                                                         const float *tbt, float *u, float *S, float *uq, float *y,
                                                         const float *mq, const float *idv, const float *x,
                                                         const float *r, const float *q, const float *p, float alpha,
-                                                        float beta, float *evec) {
+                                                        float beta, float *evec, float &dot) {
     const int nbatch = (m.ne + NBF - 1) / NBF;
     constexpr int MQT = (CXF * NQ + TC - 1) / TC;   // mass-data values per thread (blockDim == TC)
     for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
@@ -770,15 +782,20 @@ struct Family {
       }
       __syncthreads();
       interp_p<DIM, Q, D, CXF>(uq, y, S, tbt);
-      for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) evec[(size_t)e0 * DIM * ND + k] = y[k];
+      for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) {
+        const float yk = y[k];
+        evec[(size_t)e0 * DIM * ND + k] = yk;
+        dot = fmaf(u[k], yk, dot);
+      }
       __syncthreads();
     }
   }
 
   static constexpr size_t cg_smem() { return sizeof(double) * (TAB + CXC * ND + MC_S + CXC * NQ + CXC * ND + RED); }
-  // Standard Jacobi PCG, three grid barriers per iteration. (A one-reduction
-  // variant with a scalar recurrence for beta saves a barrier but costs ~5 %
-  // more FP64 operations, which is slower on this FP64-bound kernel.)
+  // Jacobi PCG with the standard recurrences and two grid barriers per
+  // iteration: p.Mp is summed element by element inside the element sweep
+  // (u_e . M_e u_e), so alpha is known after the first barrier and a single node
+  // sweep gathers q, updates p, x, r, z and forms r.r and r.z.
   static __device__ __forceinline__ void body_cg(CgArgs a) {
     extern __shared__ double sm[];
     double *st = sm, *u = st + TAB, *S = u + CXC * ND, *uq = S + MC_S, *y = uq + CXC * NQ, *red = y + CXC * ND;
@@ -867,12 +884,26 @@ struct Family {
       __syncthreads();
       const double beta = s_sc[5];
       rz_old = rz;
-      // E-vector of M p_new, p_new = z + beta p (z = invdiag r, stored by the r update)
-      sweep_matvec<4, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.z, a.r, a.ap, a.p, 0.0, beta,
-                              a.evec);
+      // E-vector of M p_new, p_new = z + beta p (z = invdiag r, stored by the r update),
+      // and p_new . M p_new summed element by element (p_new = 0 on constrained DOFs)
+      {
+        double pq = 0.0;
+        sweep_matvec<4, double>(m, s_eb, tb, tbt, u, S, uq, y, a.mq, a.invdiag, a.z, a.r, a.ap, a.p, 0.0, beta,
+                                a.evec, &pq);
+        double acc[1] = {pq};
+        bsum<1>(acc, red);
+        if (threadIdx.x == 0) a.partials[(size_t)3 * G + blockIdx.x] = acc[0];
+      }
       if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
-      {  // q = M p_new, p = p_new, p.q (all loads of a node before any use)
-        double acc[1] = {0.0};
+      if (threadIdx.x < 32) {
+        const double v = warp_sum_partials(a.partials + (size_t)3 * G, G);
+        if (threadIdx.x == 0) s_sc[4] = rz / v;   // alpha, once per block
+      }
+      __syncthreads();
+      const double alpha = s_sc[4];
+      {  // one node sweep: q = M p_new gathered, p = p_new, x += alpha p, r -= alpha q,
+         // z = invdiag r, r.r and r.z (all loads of a component before any use)
+        double acc[2] = {0.0, 0.0};
         for (int g = gtid; g < nh1; g += gstride) {
           int off[1 << DIM] = {};
           const int n = node_copies<DIM, D>(m, g, DIM, off);
@@ -887,6 +918,7 @@ struct Family {
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {   // one component's copies at a time (register budget)
             const int k = c * nh1 + g;
+            const double xv = a.x[k], rv = a.r[k];
             double ev[1 << DIM];
 #pragma unroll
             for (int j = 0; j < (1 << DIM); ++j) ev[j] = j < n ? a.evec[off[j] + c * ND] : 0.0;
@@ -894,48 +926,12 @@ struct Family {
 #pragma unroll
             for (int j = 1; j < (1 << DIM); ++j)
               if (j < n) qv += ev[j];
-            double pn = 0.0;
-            if (idg[c] != 0.0) {
-              pn = fma(beta, pv[c], zv[c]);
-              acc[0] = fma(pn, qv, acc[0]);
-            } else {
-              qv = 0.0;
-            }
-            a.ap[k] = qv;
-            a.p[k] = pn;
-          }
-        }
-        bsum<1>(acc, red);
-        if (threadIdx.x == 0) a.partials[(size_t)3 * G + blockIdx.x] = acc[0];
-      }
-      if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
-      if (threadIdx.x < 32) {
-        const double v = warp_sum_partials(a.partials + (size_t)3 * G, G);
-        if (threadIdx.x == 0) s_sc[4] = rz / v;   // alpha, once per block
-      }
-      __syncthreads();
-      const double alpha = s_sc[4];
-      {  // x += alpha p, r -= alpha q, r.r, r.z (two DOFs per step, loads first)
-        double acc[2] = {0.0, 0.0};
-        const int nt = DIM * nh1;
-        for (int k0 = gtid; k0 < nt; k0 += 2 * gstride) {
-          double idg[2], pv[2], xv[2], qv[2], rv[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int k = k0 + h * gstride < nt ? k0 + h * gstride : k0;
-            idg[h] = __ldg(a.invdiag + k);
-            pv[h] = a.p[k];
-            xv[h] = a.x[k];
-            qv[h] = a.ap[k];
-            rv[h] = a.r[k];
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int k = k0 + h * gstride;
-            if (k < nt && idg[h] != 0.0) {
-              a.x[k] = fma(alpha, pv[h], xv[h]);
-              const double r2 = fma(-alpha, qv[h], rv[h]);
-              const double z2 = r2 * idg[h];
+            if (idg[c] != 0.0) {   // constrained DOFs keep p = r = z = 0
+              const double pn = fma(beta, pv[c], zv[c]);
+              const double r2 = fma(-alpha, qv, rv);
+              const double z2 = r2 * idg[c];
+              a.p[k] = pn;
+              a.x[k] = fma(alpha, pn, xv);
               a.r[k] = r2;
               a.z[k] = z2;
               acc[0] = fma(r2, r2, acc[0]);
@@ -987,16 +983,17 @@ struct Family {
             tb[k] = (float)(k < Q * D ? st[oB + k] : st[oBt + k - Q * D]);
           __syncthreads();
         },
-        [&](float beta) {
+        [&](float beta, float &pq) {
           sweep_matvec_f<3>(a.mesh, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32,
-                            a.p32, 0.0f, beta, a.evec32);
+                            a.p32, 0.0f, beta, a.evec32, pq);
           return true;
         });
   }
 
   // The refinement loop shared by the CUDA-core (body_cg_ir) and tensor-core
   // (lh_tc.cuh) inner solvers: inner_begin() runs before each inner solve,
-  // inner_sweep(beta) writes the FP32 E-vector of M p_new (false: a bounded
+  // inner_sweep(beta, pq) writes the FP32 E-vector of M p_new and adds this
+  // thread's share of p_new . M p_new to pq (false: a bounded
   // device wait gave up). st/u/S/uq/y: FP64 sweep space; RELOAD_TAB: the
   // FP64 tables share space with the inner sweep and are reloaded per refinement.
   template <bool RELOAD_TAB, class Begin, class Sweep>
@@ -1139,22 +1136,38 @@ struct Family {
         if (rr <= target || it >= a.max_inner) break;
         const float beta = it == 0 ? 0.0f : rz / rz_old;
         rz_old = rz;
-        // E: FP32 E-vector of M p_new, p_new = invdiag r + beta p
-        const bool swept = inner_sweep(beta);
-        if (!swept || !sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
-        {  // q = M p_new gathered, p = p_new, p.q
-          // (all loads of a node issued before any use: the sweep is latency-bound)
+        // E: FP32 E-vector of M p_new, p_new = invdiag r + beta p, and p_new . M p_new
+        // summed element by element inside the sweep
+        {
+          float pq = 0.0f;
+          const bool swept = inner_sweep(beta, pq);
+          float acc[5] = {pq, 0, 0, 0, 0};
+          block_sum_f(acc);
+          if (threadIdx.x == 0) pf[(size_t)2 * G + blockIdx.x] = acc[0];
+          if (!swept || !sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
+        }
+        if (threadIdx.x < 32) {
+          float t = 0.0f;
+          for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)2 * G + i];
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (threadIdx.x == 0) s_f[2] = rz / t;
+        }
+        __syncthreads();
+        const float alpha = s_f[2];
+        {  // one node sweep: q = M p_new gathered, p = p_new, d += alpha p, r -= alpha q,
+           // r.r and r.z (all loads of a node issued before any use)
           float acc[5] = {0, 0, 0, 0, 0};
           for (int g = gtid; g < nh1; g += gstride) {
             int off[1 << DIM] = {};
             const int n = node_copies<DIM, D>(m, g, DIM, off);
-            float idg[DIM], pv[DIM], rv[DIM], ev[DIM][1 << DIM];
+            float idg[DIM], pv[DIM], rv[DIM], dv[DIM], ev[DIM][1 << DIM];
 #pragma unroll
             for (int c = 0; c < DIM; ++c) {
               const int k = c * nh1 + g;
               idg[c] = __ldg(a.invdiag32 + k);
               pv[c] = a.p32[k];
               rv[c] = a.r32[k];
+              dv[c] = a.d32[k];
 #pragma unroll
               for (int j = 0; j < (1 << DIM); ++j) ev[c][j] = j < n ? a.evec32[off[j] + c * ND] : 0.0f;
             }
@@ -1165,52 +1178,14 @@ struct Family {
 #pragma unroll
               for (int j = 1; j < (1 << DIM); ++j)
                 if (j < n) qv += ev[c][j];
-              float pn = 0.0f;
-              if (idg[c] != 0.0f) {
-                pn = fmaf(beta, pv[c], idg[c] * rv[c]);
-                acc[0] = fmaf(pn, qv, acc[0]);
-              } else {
-                qv = 0.0f;
-              }
-              a.ap32[k] = qv;
-              a.p32[k] = pn;
-            }
-          }
-          block_sum_f(acc);
-          if (threadIdx.x == 0) pf[(size_t)2 * G + blockIdx.x] = acc[0];
-        }
-        if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
-        if (threadIdx.x < 32) {
-          float t = 0.0f;
-          for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)2 * G + i];
-          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          if (threadIdx.x == 0) s_f[2] = rz / t;
-        }
-        __syncthreads();
-        const float alpha = s_f[2];
-        {  // d += alpha p, r -= alpha q, r.r, r.z (four DOFs per step, loads first)
-          float acc[5] = {0, 0, 0, 0, 0};
-          const int nt = DIM * nh1;
-          for (int k0 = gtid; k0 < nt; k0 += 4 * gstride) {
-            float idg[4], pv[4], dv[4], qv[4], rv[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const int k = k0 + h * gstride < nt ? k0 + h * gstride : k0;
-              idg[h] = __ldg(a.invdiag32 + k);
-              pv[h] = a.p32[k];
-              dv[h] = a.d32[k];
-              qv[h] = a.ap32[k];
-              rv[h] = a.r32[k];
-            }
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const int k = k0 + h * gstride;
-              if (k < nt && idg[h] != 0.0f) {
-                a.d32[k] = fmaf(alpha, pv[h], dv[h]);
-                const float r2 = fmaf(-alpha, qv[h], rv[h]);
+              if (idg[c] != 0.0f) {   // constrained DOFs keep p = r = d = 0
+                const float pn = fmaf(beta, pv[c], idg[c] * rv[c]);
+                const float r2 = fmaf(-alpha, qv, rv[c]);
+                a.p32[k] = pn;
+                a.d32[k] = fmaf(alpha, pn, dv[c]);
                 a.r32[k] = r2;
                 acc[0] = fmaf(r2, r2, acc[0]);
-                acc[1] = fmaf(r2 * idg[h], r2, acc[1]);
+                acc[1] = fmaf(r2 * idg[c], r2, acc[1]);
               }
             }
           }

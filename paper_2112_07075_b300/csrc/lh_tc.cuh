@@ -141,8 +141,10 @@ struct TcMass {
 
   // FP32 E-vector of M u for u = p_new = invdiag r + beta p (MODE 3, the inner
   // sweep) or u = d32 masked to the free DOFs (MODE 0).
+  // pq: this thread's share of u . M u = sum_e sum_q mq (B u_e)_q^2, formed from the
+  // interpolated values it scales (the GEMM1 output).
   template <int MODE>
-  __device__ bool sweep(const CgIrArgs &a, float beta) {
+  __device__ bool sweep(const CgIrArgs &a, float beta, float &pq) {
     const MeshDesc &m = a.mesh;
     const int rows_total = 3 * m.ne;
     const int ntiles = (rows_total + L::ROWS - 1) / L::ROWS;
@@ -274,6 +276,8 @@ struct TcMass {
               z[2] = yv[8 * h + 2] * m0.z; z[3] = yv[8 * h + 3] * m0.w;
               z[4] = yv[8 * h + 4] * m1.x; z[5] = yv[8 * h + 5] * m1.y;
               z[6] = yv[8 * h + 6] * m1.z; z[7] = yv[8 * h + 7] * m1.w;
+#pragma unroll
+              for (int l = 0; l < 8; ++l) pq = fmaf(yv[8 * h + l], z[l], pq);
             } else {
 #pragma unroll
               for (int l = 0; l < 8; ++l) z[l] = 0.0f;
@@ -293,6 +297,8 @@ struct TcMass {
             const float4 m1 = *reinterpret_cast<const float4 *>(mrow + qc + 4);
             z[0] = yv[0] * m0.x; z[1] = yv[1] * m0.y; z[2] = yv[2] * m0.z; z[3] = yv[3] * m0.w;
             z[4] = yv[4] * m1.x; z[5] = yv[5] * m1.y; z[6] = yv[6] * m1.z; z[7] = yv[7] * m1.w;
+#pragma unroll
+            for (int l = 0; l < 8; ++l) pq = fmaf(yv[l], z[l], pq);
           } else {
 #pragma unroll
             for (int l = 0; l < 8; ++l) z[l] = 0.0f;
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(512, 1) k_cg_tc(CgIrArgs a) {
   double *red = reinterpret_cast<double *>(tcm.mqs + L::MQB);
   if (ok)
     F::template cg_ir_core<true>(
-        a, st, u, S, uq, y, red, s_eb, [&]() {}, [&](float beta) { return tcm.template sweep<3>(a, beta); });
+        a, st, u, S, uq, y, red, s_eb, [&]() {}, [&](float beta, float &pq) { return tcm.template sweep<3>(a, beta, pq); });
   tcm.end(a);
 }
 
@@ -390,7 +396,8 @@ __global__ void __launch_bounds__(512, 1) k_tc_apply(CgIrArgs a) {
   __shared__ uint32_t s_tmem;
   __shared__ int s_base[L::ROWS];
   TcMass<P, Q> tcm;
-  if (tcm.begin(a, base, bars, &s_tmem, s_base)) tcm.template sweep<0>(a, 0.0f);
+  float unused = 0.0f;
+  if (tcm.begin(a, base, bars, &s_tmem, s_base)) tcm.template sweep<0>(a, 0.0f, unused);
   tcm.end(a);
 }
 
