@@ -310,9 +310,10 @@ def run_ours(args):
     batching = None
     learned = None
     if not args.no_forms and world == 1:
-        forms = forms_report(flush)
-        batching = batching_report(flush)
-        learned = learned_report(flush)
+        which = ("precision", "batching", "learned") if args.forms == "all" else (args.forms,)
+        forms = forms_report(flush) if "precision" in which else None
+        batching = batching_report(flush) if "batching" in which else None
+        learned = learned_report(flush) if "learned" in which else None
     clk.__exit__()
     clocks = clk.summary()
     clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
@@ -320,7 +321,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32(inner CG)",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32_ir": "f64+f32(inner CG)", "bf16tc_ir": "f64+bf16(tensor-core inner CG)"}[args.precision],
             "data": "synthetic",
             "config": {"workload": wl["desc"], "precision": args.precision, "dim": dim, "n": n, "order": p, "q1": q1, "cfl": wl["cfl"],
                        "t_end": wl["t_end"], "nv_per_gpu": sz.nv, "ne": sz.ne, "nq": sz.nq,
@@ -645,6 +646,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms", default="all", choices=["all", "precision", "batching", "learned"],
+                    help="which form reports to add (default all; --no-forms for none)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "bf16tc_ir"],
                     help="mass-solve precision of the main arm (the headline workload is FP64)")
     args = ap.parse_args()

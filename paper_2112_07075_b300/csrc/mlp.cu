@@ -254,12 +254,11 @@ bool gemm(GemmArgs g, cudaStream_t s) {
   const bool okB = BL == B_NMAJOR ? make_tmap(&tb, g.B, g.K, g.N, g.ldb, kBK, BN)
                                   : make_tmap(&tb, g.B, g.N, g.K, g.ldb, 64, kBK);
   if (!okA || !okB) return false;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute((const void *)k_gemm<AL, BL, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         GemmCfg<BN>::SMEM);
-    attr = true;
-  }
+  // the shared-memory opt-in, once per instantiation (thread-safe static init)
+  static const bool attr = cudaFuncSetAttribute((const void *)k_gemm<AL, BL, BN>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                GemmCfg<BN>::SMEM) == cudaSuccess;
+  if (!attr) return false;
   if (g.splits < 1) g.splits = 1;
   dim3 grid((g.N + BN - 1) / BN, (g.M + 127) / 128, g.splits);
   k_gemm<AL, BL, BN><<<grid, 128, GemmCfg<BN>::SMEM, s>>>(ta, tb, g);
