@@ -219,15 +219,15 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
-  if (!fn) {
+  static const EncodeFn fn = []() -> EncodeFn {   // resolved once (thread-safe static init)
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
-  }
+      return reinterpret_cast<EncodeFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 bool make_tmap(CUtensorMap *tm, const void *ptr, int inner, int outer, int pitch_elems, int box_inner, int box_outer) {
