@@ -180,6 +180,17 @@ def test_cfl_controlled_steps_match_oracle(dim, n, p, q1, jit):
         assert _field_err(a, b) < STEP_TOL
 
 
+def test_long_horizon_200_cfl_steps_match_oracle():
+    """3D Taylor-Green 4^3 Q2/Q1 (jittered), 200 CFL steps (t ~ 0.25): no slow drift of the
+    GPU solution away from the oracle; the CG tolerance (1e-12) enters every stage, so
+    the bar is 1e-10 per field after this many steps."""
+    hy, (xo, vo, eo, t, oi), (xg, vg, eg, si) = _run_steps(3, 4, 2, 4, 0.1, 200, None, t_end=10.0)
+    assert si.status == 0 and si.steps == 200
+    assert abs(si.t - t) <= 1e-12 * t
+    for a, b in ((xg, xo), (vg, vo), (eg, eo)):
+        assert _field_err(a, b) < 1e-10
+
+
 def test_gresho_steps_match_oracle():
     hy, (xo, vo, eo, t, _), (xg, vg, eg, si) = _run_steps(2, 10, 2, 4, 0.0, 5, 1e-3, -0.5, 0.5, "gresho")
     for a, b in ((xg, xo), (vg, vo), (eg, eo)):
