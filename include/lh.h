@@ -238,6 +238,56 @@ lh_status lh_timing_enable(lh_ctx *ctx, int enable);
 lh_status lh_timing_read(lh_ctx *ctx, double *solver_ms, int *solves);
 
 /* ---------------------------------------------------------------------------
+ * Remap phase, velocity (Section 3.5; the continuous advection of Section 2.3).
+ *
+ * The remap moves the velocity from the mesh at the H1 node positions x0 to the
+ * mesh at x1 (same topology) by integrating, over the pseudo-time tau in [0, 1]
+ * with the mesh moving as x(tau) = x0 + tau u, u = x1 - x0,
+ *     M(tau) dv/dtau = K(tau) v,
+ *     M(tau)_ij = int w_i w_j dx,   K(tau)_ij = int w_i (u . grad w_j) dx
+ * (unit density; the scalar matrices act on each component). Both operators are
+ * partially assembled: per stage one element pass computes omega detJ(tau) and
+ * omega adj(J(tau)) u at the quadrature points and applies K element by element
+ * with sum factorization; M(tau) is inverted by the Lagrange phase's persistent
+ * Jacobi-PCG (FP64 whatever the context's precision).
+ * ------------------------------------------------------------------------- */
+
+/* Result of one lh_remap_velocity call; lives in DEVICE memory, reset by the call. */
+typedef struct {
+  int status;             /* LH_OK or the context's latched device status (first error
+                             since the last lh_sync_status): LH_ERR_INVERTED when
+                             det J(tau) <= 0 at a qpoint, or a solver status */
+  int solves;             /* mass solves taken (2 per pseudo-time step) */
+  int cg_iters_max;       /* largest iteration count of one solve */
+  int reserved;
+  long long cg_iters_total;
+  double cg_rel_res_max;  /* largest final relative residual of one solve */
+} lh_remap_info;
+
+/* Remap the velocity v (DEVICE [dim][N_H1], updated in place) from the node
+ * positions x0 to x1 (DEVICE [dim][N_H1]) with `steps` >= 1 equal pseudo-time
+ * steps h = 1/steps of the explicit midpoint rule:
+ *     k1 = M(tau)^-1 K(tau) v,   k2 = M(tau + h/2)^-1 K(tau + h/2) (v + h/2 k1),
+ *     v <- v + h k2.
+ * constrained != 0: the Lagrange phase's v.n = 0 DOFs keep their value (the solves
+ * act on the free DOFs); 0: every DOF is remapped. Mass solves: FP64 Jacobi-PCG to
+ * rel_tol (<= 0: 1e-12) and max_it (<= 0: 1000), warm-started from the previous
+ * stage's rate. info: DEVICE lh_remap_info or NULL.
+ * Works in the context's solver and stage scratch and in its force quadrature data
+ * buffer: call lh_update_qdata again before a later lh_force_mult/lh_force_mult_t.
+ * v must not alias x0 or x1 (LH_ERR_ARG). */
+lh_status lh_remap_velocity(lh_ctx *ctx, const double *x0, const double *x1, double *v, int steps,
+                            int constrained, double rel_tol, int max_it, lh_remap_info *info,
+                            lh_stream_t stream);
+
+/* The remap operators at one pseudo-time, without boundary conditions:
+ * kv = K(tau) v and mv = M(tau) v on the mesh x0 + tau (x1 - x0). kv or mv may be
+ * NULL. All DEVICE [dim][N_H1]; kv and mv must not alias v (LH_ERR_ARG). Uses the
+ * same context scratch as lh_remap_velocity. */
+lh_status lh_remap_apply(lh_ctx *ctx, const double *x0, const double *x1, double tau, const double *v,
+                         double *kv, double *mv, lh_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Batching form: many independent problems advanced together.
  *
  * A batch references existing contexts (2D, q1 = 2*order, LH_PRECISION_FP64;

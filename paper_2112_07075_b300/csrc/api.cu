@@ -251,6 +251,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
                    o.k_geom,  o.k_diag,  o.k_emass,   o.k_init_e, o.k_cg_ir};
   for (int k = 0; k < 10; ++k)
     LH_CUDA(c, cudaFuncSetAttribute(kerns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smems[k]));
+  LH_CUDA(c, cudaFuncSetAttribute(o.k_remap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_remap));
   c->grid_elem = (m.ne + o.nb - 1) / o.nb;
   int occ = 0;
   LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, o.k_cg, o.threads_cg, o.smem_cg));
@@ -319,6 +320,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   c->counter = (unsigned int *)ctl;
   c->bar = (GridBarrier *)(ctl + 64);
   c->dstatus = (int *)(ctl + 128);
+  c->remap_ci = (lh_cg_info *)(ctl + 192);
 
   // ---- tables, vertices, node positions
   std::vector<double> tab(tablen);
@@ -516,9 +518,12 @@ constexpr double kInnerTolTc = 1e-4; // tensor-core inner solve (BF16 hi/lo oper
 constexpr int kMaxOuter = 40;
 constexpr int kMaxInner = 200;
 
+// mq_r, inv_r: mass data and Jacobi inverse of another mass matrix on the same mesh
+// topology (the remap's M(tau)); the solve then runs the FP64 solver with them.
 static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
-                           int *iters_out, double *relres_out, cudaStream_t s) {
-  if (c->prm.precision == LH_PRECISION_FP32_IR || c->prm.precision == LH_PRECISION_BF16TC_IR) {
+                           int *iters_out, double *relres_out, cudaStream_t s, const double *mq_r,
+                           const double *inv_r) {
+  if (!mq_r && (c->prm.precision == LH_PRECISION_FP32_IR || c->prm.precision == LH_PRECISION_BF16TC_IR)) {
     const bool tcf = c->prm.precision == LH_PRECISION_BF16TC_IR;
     CgIrArgs a{};
     a.mesh = c->mesh;
@@ -554,8 +559,8 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
   CgArgs a{};
   a.mesh = c->mesh;
   a.tab = c->tab;
-  a.mq = c->mq;
-  a.invdiag = c->invdiag;
+  a.mq = mq_r ? mq_r : c->mq;
+  a.invdiag = mq_r ? inv_r : c->invdiag;
   a.b = b;
   a.x = x;
   a.r = c->r;
@@ -579,11 +584,12 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
 // Every mass solve goes through here; with the timing probe on, a pair of events
 // brackets the solver launch on its stream.
 static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
-                         int *iters_out, double *relres_out, cudaStream_t s) {
+                         int *iters_out, double *relres_out, cudaStream_t s, const double *mq_r = nullptr,
+                         const double *inv_r = nullptr) {
   const bool rec = c->timing && c->timing_n < lh_ctx::kTimingPairs;
   if (rec && cudaEventRecord(c->tev[2 * c->timing_n], s) != cudaSuccess)
     return fail(c, LH_ERR_CUDA, "timing event record");
-  const lh_status st = cg_launch(c, b, x, tol, max_it, info, iters_out, relres_out, s);
+  const lh_status st = cg_launch(c, b, x, tol, max_it, info, iters_out, relres_out, s, mq_r, inv_r);
   if (st != LH_OK) return st;
   if (rec) {
     if (cudaEventRecord(c->tev[2 * c->timing_n + 1], s) != cudaSuccess)
@@ -720,6 +726,151 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
   if (lh_status st = check_launch(c, "force_t 2")) return st;
   k_step_finish<<<1, 1, 0, s>>>(info, c->dstatus, src ? 1 : 0);
   return check_launch(c, "step finish");
+}
+
+// ---------------------------------------------------------------------------
+// Remap phase, velocity (Section 3.5)
+// ---------------------------------------------------------------------------
+// Scratch of a remap call (all of it free between Lagrange steps): the stage rate k
+// and the displacement in the RK2 stage vectors, M(tau)'s Jacobi inverse in vb, its
+// mass data and element diagonal in the force quadrature data buffer.
+struct RemapScratch {
+  double *u, *k, *inv, *mq, *dvec;
+};
+static RemapScratch remap_scratch(lh_ctx *c) {
+  return {c->xh, c->vh, c->vb, c->D, c->D + (size_t)c->mesh.ne * c->nq};
+}
+// mq [NE][NQ] and the element diagonal [NE][ND] must fit in the quadrature data
+// buffer [NE][dim*dim][NQ]: (dim^2 - 1) q1^dim >= (p+1)^dim, true for q1 >= p+1
+static bool remap_fits(const lh_ctx *c) { return (size_t)(c->dim * c->dim - 1) * c->nq >= (size_t)c->nd; }
+
+}  // extern "C"
+namespace {
+__global__ void k_diff(size_t n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ d) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    d[k] = a[k] - b[k];
+}
+__global__ void k_axpy(size_t n, double a, const double *__restrict__ x, double *__restrict__ y) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    y[k] = fma(a, x[k], y[k]);
+}
+__global__ void k_remap_info_reset(lh_remap_info *info) {
+  info->status = 0;
+  info->solves = 0;
+  info->cg_iters_max = 0;
+  info->reserved = 0;
+  info->cg_iters_total = 0;
+  info->cg_rel_res_max = 0.0;
+}
+// After each remap solve: folds the solve's result into the record. Its status is
+// the context's latched status (first device error since the last lh_sync_status:
+// an inverted element found by an element pass, a solver failure), as for
+// lh_step_info.
+__global__ void k_remap_solved(lh_remap_info *info, const lh_cg_info *ci, const int *dstatus) {
+  info->solves += 1;
+  info->cg_iters_total += ci->iters;
+  info->cg_iters_max = max(info->cg_iters_max, ci->iters);
+  info->cg_rel_res_max = fmax(info->cg_rel_res_max, ci->rel_res);
+  if (info->status == 0) info->status = *dstatus;
+}
+}  // namespace
+extern "C" {
+
+// One stage: element pass on x(tau) with input w = v + s k, node pass (rhs = K w,
+// Jacobi inverse of M(tau)), then k = M(tau)^-1 K w warm-started from k.
+static lh_status remap_stage(lh_ctx *c, const RemapScratch &r, const double *x0, const double *v, double tau,
+                             double sk, int constrained, double tol, int max_it, lh_cg_info *ci,
+                             lh_remap_info *info, cudaStream_t s) {
+  RemapArgs a{};
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.x0 = x0;
+  a.u = r.u;
+  a.v = v;
+  a.k = sk != 0.0 ? r.k : nullptr;
+  a.s = sk;
+  a.tau = tau;
+  a.mq = r.mq;
+  a.evec = c->evec;
+  a.dvec = r.dvec;
+  a.status = c->dstatus;
+  c->ops->remap(a, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "remap element pass")) return st;
+  c->ops->remap_nodes(c->mesh, c->evec, r.dvec, constrained, c->rhs, r.inv, c->grid_node, kNodeThreads, s);
+  if (lh_status st = check_launch(c, "remap node pass")) return st;
+  if (lh_status st = cg_impl(c, c->rhs, r.k, tol, max_it, ci, nullptr, nullptr, s, r.mq, r.inv)) return st;
+  if (!info) return LH_OK;
+  k_remap_solved<<<1, 1, 0, s>>>(info, ci, c->dstatus);
+  return check_launch(c, "remap info");
+}
+
+lh_status lh_remap_velocity(lh_ctx *ctx, const double *x0, const double *x1, double *v, int steps,
+                            int constrained, double rel_tol, int max_it, lh_remap_info *info,
+                            lh_stream_t stream) {
+  if (!ctx || !x0 || !x1 || !v) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (steps < 1) return fail(ctx, LH_ERR_ARG, "steps must be >= 1");
+  if (!remap_fits(ctx)) return fail(ctx, LH_ERR_UNSUPPORTED, "remap scratch does not fit (q1 < p+1)");
+  if (v == x0 || v == x1) return fail(ctx, LH_ERR_ARG, "v must not alias x0 or x1");
+  if (!(rel_tol == rel_tol)) return fail(ctx, LH_ERR_ARG, "bad tolerance");
+  if (rel_tol <= 0.0) rel_tol = 1e-12;
+  if (max_it <= 0) max_it = 1000;
+  lh_ctx *c = ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  const RemapScratch r = remap_scratch(c);
+  lh_cg_info *ci = c->remap_ci;
+  k_diff<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x1, x0, r.u);
+  if (lh_status st = check_launch(c, "remap displacement")) return st;
+  LH_CUDA(c, cudaMemsetAsync(r.k, 0, c->nv * sizeof(double), s));
+  if (info) {
+    k_remap_info_reset<<<1, 1, 0, s>>>(info);
+    if (lh_status st = check_launch(c, "remap info")) return st;
+  }
+  const double h = 1.0 / steps;
+  for (int n = 0; n < steps; ++n) {
+    const double tau = n * h;
+    if (lh_status st = remap_stage(c, r, x0, v, tau, 0.0, constrained, rel_tol, max_it, ci, info, s)) return st;
+    if (lh_status st = remap_stage(c, r, x0, v, tau + 0.5 * h, 0.5 * h, constrained, rel_tol, max_it, ci, info, s))
+      return st;
+    k_axpy<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, h, r.k, v);
+    if (lh_status st = check_launch(c, "remap update")) return st;
+  }
+  return LH_OK;
+}
+
+lh_status lh_remap_apply(lh_ctx *ctx, const double *x0, const double *x1, double tau, const double *v,
+                         double *kv, double *mv, lh_stream_t stream) {
+  if (!ctx || !x0 || !x1 || !v) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (kv == v || mv == v || (kv && kv == mv)) return fail(ctx, LH_ERR_ARG, "kv and mv must not alias v or each other");
+  if (!remap_fits(ctx)) return fail(ctx, LH_ERR_UNSUPPORTED, "remap scratch does not fit (q1 < p+1)");
+  lh_ctx *c = ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  const RemapScratch r = remap_scratch(c);
+  k_diff<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x1, x0, r.u);
+  if (lh_status st = check_launch(c, "remap displacement")) return st;
+  RemapArgs a{};
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.x0 = x0;
+  a.u = r.u;
+  a.v = v;
+  a.tau = tau;
+  a.mq = r.mq;
+  a.evec = kv ? c->evec : nullptr;
+  a.status = c->dstatus;
+  c->ops->remap(a, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "remap element pass")) return st;
+  if (kv) {
+    c->ops->remap_nodes(c->mesh, c->evec, nullptr, 0, kv, nullptr, c->grid_node, kNodeThreads, s);
+    if (lh_status st = check_launch(c, "remap node pass")) return st;
+  }
+  if (mv) {
+    MassArgs ma{c->mesh, c->tab, r.mq, v, c->evec};
+    c->ops->mass(ma, c->grid_elem, s);
+    if (lh_status st = check_launch(c, "remap mass")) return st;
+    c->ops->gather(c->mesh, c->evec, c->dim, mv, 1.0, nullptr, c->grid_node, kNodeThreads, s);
+    if (lh_status st = check_launch(c, "remap mass gather")) return st;
+  }
+  return LH_OK;
 }
 
 }  // extern "C"

@@ -112,6 +112,18 @@ struct EmassArgs {
   double *me_inv;
 };
 
+// Remap phase (Section 3.5): one stage's element pass on the mesh x(tau) = x0 + tau u.
+struct RemapArgs {
+  MeshDesc mesh;
+  const double *tab, *x0, *u;  // H1 [DIM][N_H1]: source positions, displacement x1 - x0
+  const double *v, *k;         // stage input w = v + s k (k may be NULL: w = v)
+  double s, tau;
+  double *mq;                  // out [NE][NQ]: omega detJ(tau)
+  double *evec;                // out [NE][DIM][ND]: element contributions of K(tau) w, or NULL
+  double *dvec;                // out [NE][ND]: element diagonal of M(tau), or NULL
+  int *status;
+};
+
 struct InitEArgs {
   MeshDesc mesh;
   const double *tab, *x0, *mq, *rho0, *me_inv;
@@ -149,6 +161,13 @@ struct Ops {
   // M x with the tensor-core element operator: x = a.d32 (free DOFs), E-vector in
   // a.evec32, node sums in a.ap32
   cudaError_t (*tc_apply)(CgIrArgs &, int grid, cudaStream_t);
+  // remap phase: element pass and the node pass (K w gathered into rhs, Jacobi
+  // inverse of the gathered diagonal into invdiag, 0 on constrained DOFs if asked)
+  size_t smem_remap;
+  void *k_remap;
+  void (*remap)(const RemapArgs &, int grid, cudaStream_t);
+  void (*remap_nodes)(const MeshDesc &, const double *evec, const double *dvec, int constrained, double *rhs,
+                      double *invdiag, int grid, int threads, cudaStream_t);
 };
 
 const Ops *find_ops_2d(int p, int q1);
@@ -197,6 +216,7 @@ struct lh_ctx {
   unsigned int *counter = nullptr;
   void *bar = nullptr;   // lh::GridBarrier
   int *dstatus = nullptr;
+  lh_cg_info *remap_ci = nullptr;   // result of the remap's latest mass solve
   lh_learn *learn = nullptr;   // learned-form state (lh_learn_attach), or NULL
   // solver timing probe (lh_timing_enable): event pairs around solver launches
   static constexpr int kTimingPairs = 64;

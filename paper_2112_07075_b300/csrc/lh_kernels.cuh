@@ -1385,6 +1385,98 @@ struct Family {
       a.e[(size_t)e0 * NL + k] = s;
     }
   }
+
+  // ===== remap phase (Section 3.5): one stage on the mesh x(tau) = x0 + tau u ====
+  // Per element and qpoint of x(tau): mq = omega detJ (the mass data of M(tau)) and
+  // the advection data adv_l = omega detJ (J^-1 u)_l = omega (adj(J) u)_l, kept in
+  // shared memory only. From them, in the same pass: the element diagonal of M(tau)
+  // (sum_q mq B_i(q)^2) and the element contributions of K(tau) w,
+  //     (K w)_i = sum_q B_i(q) sum_l adv_l(q) dw/dxi_l(q),   w = v + s k.
+  // smem: tab | xu[CX][ND] | uu[CX][ND] | vv[CX][ND] | S | g[DIM][CX][NQ] |
+  //       uq[CX][NQ] | adv[DIM][NB][NQ] | mqs[NB][NQ]
+  static constexpr int RM_S = max3(grad_scratch<DIM, D, Q>(CX), interp_scratch<DIM, D, Q>(CX),
+                                   interp_scratch<DIM, Q, D>(CX));
+  static constexpr size_t remap_smem() {
+    return sizeof(double) * (TAB + 3 * CX * ND + RM_S + DIM * CX * NQ + CX * NQ + DIM * NB * NQ + NB * NQ);
+  }
+  static __device__ __forceinline__ void body_remap(const RemapArgs &a, int e0) {
+    extern __shared__ double sm[];
+    double *st = sm, *xu = st + TAB, *uu = xu + CX * ND, *vv = uu + CX * ND, *S = vv + CX * ND;
+    double *g = S + RM_S, *uq = g + DIM * CX * NQ, *adv = uq + CX * NQ, *mqs = adv + DIM * NB * NQ;
+    const MeshDesc &m = a.mesh;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+      const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+      double x = 0.0, u = 0.0, w = 0.0;
+      if (b < nb) {
+        const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
+        u = a.u[gi];
+        x = fma(a.tau, u, a.x0[gi]);
+        if (a.evec) w = a.k ? fma(a.s, a.k[gi], a.v[gi]) : a.v[gi];
+      }
+      xu[k] = x;
+      uu[k] = u;
+      vv[k] = w;
+    }
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(xu, g, S, st + oB, st + oG);   // J(tau) = dx/dxi
+    interp<DIM, D, Q, CX>(uu, uq, S, st + oB);             // u at the qpoints
+    for (int k = threadIdx.x; k < NB * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      double mq = 0.0, al[DIM];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) al[l] = 0.0;
+      if (b < nb) {
+        double J[DIM * DIM], A[DIM * DIM], det;   // J[c][l] = dx_c/dxi_l, A = adj(J) = det J^-1
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int l = 0; l < DIM; ++l) J[c * DIM + l] = g[(l * CX + b * DIM + c) * NQ + q];
+        if constexpr (DIM == 2) {
+          A[0] = J[3]; A[1] = -J[1]; A[2] = -J[2]; A[3] = J[0];
+          det = J[0] * J[3] - J[1] * J[2];
+        } else {
+          A[0] = J[4] * J[8] - J[5] * J[7]; A[1] = J[2] * J[7] - J[1] * J[8]; A[2] = J[1] * J[5] - J[2] * J[4];
+          A[3] = J[5] * J[6] - J[3] * J[8]; A[4] = J[0] * J[8] - J[2] * J[6]; A[5] = J[2] * J[3] - J[0] * J[5];
+          A[6] = J[3] * J[7] - J[4] * J[6]; A[7] = J[1] * J[6] - J[0] * J[7]; A[8] = J[0] * J[4] - J[1] * J[3];
+          det = J[0] * A[0] + J[1] * A[3] + J[2] * A[6];
+        }
+        if (!(det > 0.0)) latch_status(a.status, 4);
+        double w, iw;
+        qweight(st, q, w, iw);
+        mq = w * det;
+        a.mq[(size_t)(e0 + b) * NQ + q] = mq;
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) {
+          double s = 0.0;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) s = fma(A[l * DIM + c], uq[(b * DIM + c) * NQ + q], s);
+          al[l] = w * s;
+        }
+      }
+      mqs[k] = mq;
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) adv[l * NB * NQ + k] = al[l];
+    }
+    __syncthreads();
+    if (a.dvec) {
+      interp<DIM, Q, D, NB>(mqs, xu, S, st + oB2t);   // sum_q mq B_i(q)^2
+      for (int k = threadIdx.x; k < nb * ND; k += blockDim.x) a.dvec[(size_t)e0 * ND + k] = xu[k];
+    }
+    if (!a.evec) return;
+    grad_ref<DIM, D, Q, CX>(vv, g, S, st + oB, st + oG);   // dw/dxi
+    for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
+      const int q = k % NQ, bc = k / NQ, b = bc / DIM;
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) s = fma(adv[(l * NB + b) * NQ + q], g[(l * CX + bc) * NQ + q], s);
+      uq[k] = s;
+    }
+    __syncthreads();
+    interp<DIM, Q, D, CX>(uq, uu, S, st + oBt);   // B^T
+    for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = uu[k];
+  }
 };
 
 // Kernel entry points (free templates; the bodies live in Family).
@@ -1408,5 +1500,7 @@ template <int DIM, int P, int Q>
 __global__ void k_emass(EmassArgs a) { Family<DIM, P, Q>::body_emass(a); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_init_e(InitEArgs a) { Family<DIM, P, Q>::body_init_e(a); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_remap(RemapArgs a) { Family<DIM, P, Q>::body_remap(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 
 }  // namespace lh

@@ -18,6 +18,22 @@ __global__ void k_gather(MeshDesc m, const double *__restrict__ evec, int C, dou
   }
 }
 
+// Remap node pass: rhs = gathered K w (C = DIM), invdiag = 1 / gathered diagonal of
+// M(tau) for every component (0 on constrained DOFs when constrained != 0).
+template <int DIM, int D>
+__global__ void k_remap_nodes(MeshDesc m, const double *__restrict__ evec, const double *__restrict__ dvec,
+                              int constrained, double *__restrict__ rhs, double *__restrict__ invdiag) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m.nh1; g += gridDim.x * blockDim.x) {
+    if (rhs)
+      for (int c = 0; c < DIM; ++c) rhs[(size_t)c * m.nh1 + g] = gather_node<DIM, D>(m, evec, DIM, c, g);
+    if (invdiag) {
+      const double inv = 1.0 / gather_node<DIM, D>(m, dvec, 1, 0, g);
+      for (int c = 0; c < DIM; ++c)
+        invdiag[(size_t)c * m.nh1 + g] = constrained && h1_constrained<DIM>(m, g, c) ? 0.0 : inv;
+    }
+  }
+}
+
 template <int DIM, int P, int Q>
 struct OpsBuilder {
   using F = Family<DIM, P, Q>;
@@ -102,6 +118,13 @@ struct OpsBuilder {
                      int grid, int threads, cudaStream_t s) {
     k_gather<DIM, P + 1><<<grid, threads, 0, s>>>(m, evec, C, out, scale, mask);
   }
+  static void remap(const RemapArgs &a, int grid, cudaStream_t s) {
+    k_remap<DIM, P, Q><<<grid, F::THREADS, F::remap_smem(), s>>>(a);
+  }
+  static void remap_nodes(const MeshDesc &m, const double *evec, const double *dvec, int constrained, double *rhs,
+                          double *invdiag, int grid, int threads, cudaStream_t s) {
+    k_remap_nodes<DIM, P + 1><<<grid, threads, 0, s>>>(m, evec, dvec, constrained, rhs, invdiag);
+  }
   static const Ops *get() {
     static const Ops ops = {DIM, P, Q, F::NB, F::THREADS, F::NBC, F::TC,
                             F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
@@ -113,7 +136,8 @@ struct OpsBuilder {
                             &gather,
                             tc_kernel(), tc_smem(), kTc ? 512 : 0, tc_img_bytes(),
                             kTc ? &cg_tc : nullptr, kTc ? &tc_image : nullptr,
-                            tc_apply_kernel(), kTc ? &tc_apply : nullptr};
+                            tc_apply_kernel(), kTc ? &tc_apply : nullptr,
+                            F::remap_smem(), (void *)k_remap<DIM, P, Q>, &remap, &remap_nodes};
     return &ops;
   }
 };

@@ -30,7 +30,8 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_sync_status",
             "lh_learn_attach",
-            "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc"]
+            "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc",
+            "lh_remap_velocity", "lh_remap_apply"]
 
 
 class LhParams(ctypes.Structure):
@@ -55,6 +56,12 @@ class LhStepInfo(ctypes.Structure):
                 ("dt_est", ctypes.c_double), ("energy_src", ctypes.c_double),
                 ("cg_rel_res", ctypes.c_double * 2), ("cg_iters", ctypes.c_int * 2),
                 ("status", ctypes.c_int), ("steps", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong)]
+
+
+class LhRemapInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("solves", ctypes.c_int), ("cg_iters_max", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong),
+                ("cg_rel_res_max", ctypes.c_double)]
 
 
 _lib = None
@@ -105,6 +112,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
         "lh_timing_enable": (I, [P, I]),
         "lh_mass_mult_tc": (I, [P, VP, VP, VP]),
+        "lh_remap_velocity": (I, [P, VP, VP, VP, I, I, D, I, VP, VP]),
+        "lh_remap_apply": (I, [P, VP, VP, D, VP, VP, VP, VP]),
         "lh_timing_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
@@ -264,6 +273,23 @@ class Context:
     def rk2avg_step(self, x, v, e, dt, info, rel_tol=1e-12, max_it=1000):
         self._check(self.lib.lh_rk2avg_step(self.h, _ptr(x), _ptr(v), _ptr(e), float(dt), float(rel_tol),
                                             int(max_it), _ptr(info), _stream()))
+
+    def new_remap_info(self):
+        import torch
+        return torch.zeros(ctypes.sizeof(LhRemapInfo), dtype=torch.uint8, device=self.device)
+
+    @staticmethod
+    def read_remap_info(buf) -> LhRemapInfo:
+        return LhRemapInfo.from_buffer_copy(buf.cpu().numpy().tobytes())
+
+    def remap_velocity(self, x0, x1, v, steps, constrained=True, rel_tol=1e-12, max_it=1000, info=None):
+        self._check(self.lib.lh_remap_velocity(self.h, _ptr(x0), _ptr(x1), _ptr(v), int(steps),
+                                               1 if constrained else 0, float(rel_tol), int(max_it), _ptr(info),
+                                               _stream()))
+
+    def remap_apply(self, x0, x1, tau, v, kv=None, mv=None):
+        self._check(self.lib.lh_remap_apply(self.h, _ptr(x0), _ptr(x1), float(tau), _ptr(v), _ptr(kv), _ptr(mv),
+                                            _stream()))
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))
