@@ -161,6 +161,16 @@ def probe_peaks():
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def run_remap_only(args):
+    """--remap-only: the remap report alone (one JSON line), for profiling the remap."""
+    import torch
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rep = remap_report(flush)
+    if not args.no_cpu_baseline:
+        rep["cpu_baseline"] = remap_cpu_baseline()
+    print(json.dumps({"remap": rep}), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -341,11 +351,13 @@ def run_ours(args):
     forms = None
     batching = None
     learned = None
+    remap = None
     if not args.no_forms and world == 1:
-        which = ("precision", "batching", "learned") if args.forms == "all" else (args.forms,)
+        which = ("precision", "batching", "learned", "remap") if args.forms == "all" else (args.forms,)
         forms = forms_report(flush) if "precision" in which else None
         batching = batching_report(flush) if "batching" in which else None
         learned = learned_report(flush) if "learned" in which else None
+        remap = remap_report(flush) if "remap" in which else None
     clk.__exit__()
     clocks = clk.summary()
     clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
@@ -368,11 +380,14 @@ def run_ours(args):
             "clocks": clocks,
             "kernels": kernels,
             "forms": {"precision": forms, "batching": batching, "learned": learned},
+            "remap": remap,
             "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
             "device_status": status, "wall_s_timed": wall,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, V)
+            if remap is not None:
+                remap["cpu_baseline"] = remap_cpu_baseline()
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -609,6 +624,139 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
     return out
 
 
+def remap_work(dim, p, q1, ne, nh1):
+    """FP64 FLOPs of one remap element pass (one stage): gradients of x(tau) and of the
+    stage input, interpolation of u, B^T of the advected gradients, the diagonal of
+    M(tau), and the pointwise work (adjugate, adv, contraction) at every qpoint."""
+    D, Q = p + 1, q1
+    if dim == 3:
+        interp = Q * D ** 3 + Q * Q * D * D + Q ** 3 * D
+        grad = 2 * Q * D ** 3 + 3 * Q * Q * D * D + 3 * Q ** 3 * D
+        point = 9 * 2 + 5 + dim * dim + dim * dim + 2   # adjugate, det, adv, contraction, weights
+    else:
+        interp = Q * D * D + Q * Q * D
+        grad = 2 * Q * D * D + 2 * Q * Q * D
+        point = 2 + dim * dim + dim * dim + 2
+    nq = Q ** dim
+    fma = ne * (2 * dim * grad + 2 * dim * interp + interp + nq * point)
+    return dict(elem_flops=2 * fma,
+                elem_bytes=8 * (3 * dim * nh1 + ne * nq + dim * ne * D ** dim + ne * D ** dim))
+
+
+def _gll_min_spacing(p):
+    """Smallest gap between the p+1 Gauss-Lobatto nodes on [0, 1] (endpoints and the
+    roots of P_p'), i.e. the first interior node."""
+    if p == 1:
+        return 1.0
+    r = np.real(np.polynomial.legendre.Legendre.basis(p).deriv().roots())
+    return float(0.5 * (1.0 + np.min(r)))
+
+
+def remap_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
+    """Velocity remap (Section 3.5) on the headline workload's mesh: after
+    `lagrange_steps` CFL steps of 3D Taylor-Green (the paper's runs remap every 50
+    cycles), remap v from the Lagrangian mesh back to the initial one. Pseudo-time
+    steps: the fewest with the largest nodal displacement per step at most half the
+    smallest GLL node spacing. Each timed remap restarts from the same v (restored
+    and the L2 flushed outside the events)."""
+    import torch
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context
+    wl = WORKLOADS[wl_name]
+    dim, n, p, q1 = wl["dim"], wl["n"], wl["order"], wl["q1"]
+    V = inputs.box_vertices(dim, n, jitter=wl["jitter"], seed=3)
+    ctx = Context(dim, n, V, p, q1, cfl=wl["cfl"])
+    x, v, e = ctx.init_state("taylor_green")
+    x_init = x.clone()
+    info = ctx.new_step_info(0.0, wl["t_end"])
+    for _ in range(lagrange_steps):
+        ctx.rk2avg_step(x, v, e, 0.0, info)
+    si = ctx.read_step_info(info)
+    hmin = _gll_min_spacing(p) / n
+    umax = float((x_init - x).abs().max().item())
+    steps = max(1, int(np.ceil(umax / (0.5 * hmin))))
+    v_lag = v.clone()
+    rinfo = ctx.new_remap_info()
+    stream = torch.cuda.current_stream()
+    ts = []
+    ctx.remap_velocity(x, x_init, v, steps, info=rinfo)      # warm-up
+    ctx.timing_enable(True)
+    ctx.timing_read()
+    solver_ms, solves, iters = 0.0, 0, 0
+    torch.cuda.nvtx.range_push("remap")   # lets a profiler select the timed remaps
+    for _ in range(reps):
+        v.copy_(v_lag)
+        flush.fill_(5.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.remap_velocity(x, x_init, v, steps, info=rinfo)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+        ms, ns = ctx.timing_read()
+        solver_ms += ms
+        solves += ns
+        iters += ctx.read_remap_info(rinfo).cg_iters_total
+    torch.cuda.nvtx.range_pop()
+    ctx.timing_enable(False)
+    ri = ctx.read_remap_info(rinfo)
+    st = ctx.sync_status()
+    sz = ctx.sizes
+    # element pass alone (K(tau) v and the data of M(tau) at one tau), events around one launch
+    W = work_model(dim, p, q1, sz.ne, sz.n_h1)
+    RW = remap_work(dim, p, q1, sz.ne, sz.n_h1)
+    kv = ctx.h1_vector()
+    te = []
+    for _ in range(reps):
+        flush.fill_(6.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.remap_apply(x, x_init, 0.5, v, kv, None)
+        b.record(stream)
+        b.synchronize()
+        te.append(a.elapsed_time(b))
+    ms_remap = statistics.mean(ts)
+    t_solver = solver_ms / max(1, solves)
+    cg_flops = iters * W["cg_iter_flops"] + solves * W["mass_flops"]
+    ctx.close()
+    return {
+        "workload": f"{wl['desc']}; v remapped from the mesh after {lagrange_steps} Lagrange CFL steps "
+                    f"(t = {si.t:.4g}) back to the initial mesh",
+        "pseudo_steps": steps, "max_displacement": umax, "min_gll_spacing": hmin,
+        "ms_per_remap": ms_remap, "ms_per_pseudo_step": ms_remap / steps,
+        "mdofs": sz.nv / (ms_remap * 1e-3) / 1e6,
+        "solves": ri.solves, "cg_iters_total": ri.cg_iters_total, "cg_iters_max": ri.cg_iters_max,
+        "cg_rel_res_max": ri.cg_rel_res_max, "status": st,
+        "solver_ms_per_solve": t_solver, "solver_share": solver_ms / max(1e-9, sum(ts)),
+        "solver_tflops": cg_flops / (solver_ms * 1e-3) / 1e12 if solver_ms > 0 else None,
+        "apply_ms": statistics.median(te),
+        "apply_note": "lh_remap_apply (displacement, one element pass with K, node gather): events "
+                      "around the call",
+        "elem_gflop_per_pass": RW["elem_flops"] / 1e9,
+        "apply_tflops": RW["elem_flops"] / (statistics.median(te) * 1e-3) / 1e12,
+        "metric_note": "mdofs = H1 vector DOFs remapped per second (one whole remap call)",
+    }
+
+
+def remap_cpu_baseline(n=12):
+    """The oracle's remap (global assembly, direct solves) on one pseudo-time step of
+    an n^3 Q2 mesh with a smooth displacement (a bounded sample: LU of the 3D mass
+    matrix at 24^3 takes more than 15 minutes)."""
+    from oracle.fem import Tables
+    from oracle.mesh import Mesh
+    from oracle.remap import Remap
+    from paper_2112_07075_b300 import inputs
+    m = Mesh(inputs.box_vertices(3, n), 3, n, 2)
+    x1 = m.x0 + 0.005 * np.sin(3.0 * m.x0)
+    R = Remap(m, Tables(3, 2, 4), x1, m.x0)
+    v = inputs.uniform(8, (3, m.NH1), -1.0, 1.0)
+    t0 = time.perf_counter()
+    R.remap(v, 1)
+    dt = time.perf_counter() - t0
+    return {"value": 3 * m.NH1 / dt / 1e6, "unit": "MDOF/s (one pseudo-step)", "cores": _cores(),
+            "kind": "oracle", "sample": f"1 pseudo-time step of a {n}^3 Q2 mesh, {dt:.1f} s"}
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -681,15 +829,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--forms", default="all", choices=["all", "precision", "batching", "learned"],
+    ap.add_argument("--forms", default="all", choices=["all", "precision", "batching", "learned", "remap"],
                     help="which form reports to add (default all; --no-forms for none)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "bf16tc_ir"],
                     help="mass-solve precision of the main arm (the headline workload is FP64)")
+    ap.add_argument("--remap-only", action="store_true",
+                    help="print only the velocity-remap report (rank 0, one GPU)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.remap_only:
+        run_remap_only(args)
     else:
         run_ours(args)
 
