@@ -227,9 +227,9 @@ def run_ours(args):
             ctx.rk2avg_step(x, v, e, 0.0, info)
             ev1[-1].record(stream)
             k += 1
-        ms, n = ctx.timing_read()
+        ms, ns = ctx.timing_read()
         solver_ms += ms
-        solver_launches += n
+        solver_launches += ns
         if trajectory:
             si_ = ctx.read_step_info(info)
             left = wl["t_end"] - si_.t
@@ -352,12 +352,15 @@ def run_ours(args):
     batching = None
     learned = None
     remap = None
+    stiffness = None
     if not args.no_forms and world == 1:
-        which = ("precision", "batching", "learned", "remap") if args.forms == "all" else (args.forms,)
+        which = ("precision", "batching", "learned", "remap", "stiffness") if args.forms == "all" \
+            else (args.forms,)
         forms = forms_report(flush) if "precision" in which else None
         batching = batching_report(flush) if "batching" in which else None
         learned = learned_report(flush) if "learned" in which else None
         remap = remap_report(flush) if "remap" in which else None
+        stiffness = stiffness_report(flush) if "stiffness" in which else None
     clk.__exit__()
     clocks = clk.summary()
     clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
@@ -381,6 +384,7 @@ def run_ours(args):
             "kernels": kernels,
             "forms": {"precision": forms, "batching": batching, "learned": learned},
             "remap": remap,
+            "stiffness": stiffness,
             "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
             "device_status": status, "wall_s_timed": wall,
         }
@@ -738,6 +742,68 @@ def remap_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
     }
 
 
+def stiffness_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
+    """Stiffness operator and discrete Laplacian (Sections 2.1, 3.3, 6) on the
+    Lagrangian mesh of the headline workload after `lagrange_steps` CFL steps:
+    PA setup on that mesh, the action S_x v, and the Laplacian -M_x^{-1} S_x v of the
+    velocity (FP64 PCG to 1e-12 from a zero guess). L2 flushed before every timed call."""
+    import torch
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context
+    wl = WORKLOADS[wl_name]
+    dim, n, p, q1 = wl["dim"], wl["n"], wl["order"], wl["q1"]
+    V = inputs.box_vertices(dim, n, jitter=wl["jitter"], seed=3)
+    ctx = Context(dim, n, V, p, q1, cfl=wl["cfl"])
+    x, v, e = ctx.init_state("taylor_green")
+    info = ctx.new_step_info(0.0, wl["t_end"])
+    for _ in range(lagrange_steps):
+        ctx.rk2avg_step(x, v, e, 0.0, info)
+    stream = torch.cuda.current_stream()
+    y, lap = ctx.h1_vector(), ctx.h1_vector()
+    cinfo = ctx.new_cg_info()
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            flush.fill_(8.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[1:])
+
+    def lap_solve():
+        lap.zero_()
+        ctx.laplacian(v, lap, 1e-12, 1000, cinfo)
+    t_setup = timed(lambda: ctx.stiffness_setup(x))
+    t_mult = timed(lambda: ctx.stiffness_mult(v, y))
+    t_lap = timed(lap_solve)
+    ci = ctx.read_cg_info(cinfo)
+    st = ctx.sync_status()
+    sz = ctx.sizes
+    D, Q = p + 1, q1
+    grad = 2 * Q * D ** 3 + 3 * Q * Q * D * D + 3 * Q ** 3 * D if dim == 3 else 2 * Q * D * D + 2 * Q * Q * D
+    nq = Q ** dim
+    ns = dim * (dim + 1) // 2
+    mult_flops = 2 * sz.ne * (2 * dim * grad + dim * nq * dim * dim)
+    mult_bytes = 8 * (sz.ne * ns * nq + 2 * sz.nv + 2 * sz.ne * dim * D ** dim)
+    W = work_model(dim, p, q1, sz.ne, sz.n_h1)
+    ctx.close()
+    return {
+        "workload": f"{wl['desc']}; Lagrangian mesh after {lagrange_steps} CFL steps, velocity field",
+        "setup_ms": t_setup, "mult_ms": t_mult, "laplacian_ms": t_lap,
+        "laplacian_cg_iters": ci.iters, "laplacian_rel_res": ci.rel_res, "status": st,
+        "mult_gflop": mult_flops / 1e9, "mult_tflops": mult_flops / (t_mult * 1e-3) / 1e12,
+        "mult_algorithmic_mb": mult_bytes / 1e6,
+        "laplacian_tflops": (mult_flops + ci.iters * W["cg_iter_flops"] + W["mass_flops"]) / (t_lap * 1e-3) / 1e12,
+        "mult_mdofs": sz.nv / (t_mult * 1e-3) / 1e6,
+        "note": "events around each call (setup: element pass + diagonal gather; mult: element pass + "
+                "node gather; laplacian: mult + FP64 PCG on M_x from zero)",
+    }
+
+
 def remap_cpu_baseline(n=12):
     """The oracle's remap (global assembly, direct solves) on one pseudo-time step of
     an n^3 Q2 mesh with a smooth displacement (a bounded sample: LU of the 3D mass
@@ -829,7 +895,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--forms", default="all", choices=["all", "precision", "batching", "learned", "remap"],
+    ap.add_argument("--forms", default="all",
+                    choices=["all", "precision", "batching", "learned", "remap", "stiffness"],
                     help="which form reports to add (default all; --no-forms for none)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "bf16tc_ir"],
                     help="mass-solve precision of the main arm (the headline workload is FP64)")

@@ -288,6 +288,38 @@ lh_status lh_remap_apply(lh_ctx *ctx, const double *x0, const double *x1, double
                          double *kv, double *mv, lh_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Stiffness (diffusion) operator of the hyper-viscosity and artificial-viscosity
+ * terms (Sections 2.1 and 3.3 name it beside the mass and force operators;
+ * Section 6 names the diffusion-integrator kernels of the viscosity calculation).
+ *
+ * On the mesh with H1 node positions x, S_ij = int grad w_i . grad w_j dx (scalar,
+ * applied to each component), partially assembled as in Section 3.1 with the
+ * reference gradients as B and, per quadrature point, the symmetric matrix
+ * G = omega det J J^-1 J^-T (omega adj(J) adj(J)^T / det J) as D; the action is
+ * sum factorized (reference gradient, G, transposed reference gradient) plus the
+ * deterministic node gather.
+ * ------------------------------------------------------------------------- */
+
+/* PA setup on the mesh at node positions x (DEVICE [dim][N_H1]): stores G
+ * ([NE][dim(dim+1)/2][q1^dim] in the context), the unit-density mass data
+ * omega det J and the Jacobi inverse of that mass matrix M_x (every DOF). An
+ * element with det J <= 0 latches LH_ERR_INVERTED in the context status. The data
+ * stays valid until the next lh_stiffness_setup. */
+lh_status lh_stiffness_setup(lh_ctx *ctx, const double *x, lh_stream_t stream);
+
+/* y = S_x u for u, y DEVICE [dim][N_H1] (must not alias), no boundary conditions.
+ * LH_ERR_ARG before the first lh_stiffness_setup. */
+lh_status lh_stiffness_mult(lh_ctx *ctx, const double *u, double *y, lh_stream_t stream);
+
+/* Discrete Laplacian of an H1 field (natural boundary conditions): lap solves
+ * M_x lap = -S_x v per component with the FP64 Jacobi-PCG on every DOF, stopping at
+ * ||b - M x||_2 <= rel_tol ||b||_2 (rel_tol <= 0: 1e-12; max_it <= 0: 1000).
+ * v, lap: DEVICE [dim][N_H1], must not alias; lap in = initial guess.
+ * info: DEVICE lh_cg_info or NULL. LH_ERR_ARG before the first lh_stiffness_setup. */
+lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol, int max_it,
+                       lh_cg_info *info, lh_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Batching form: many independent problems advanced together.
  *
  * A batch references existing contexts (2D, q1 = 2*order, LH_PRECISION_FP64;

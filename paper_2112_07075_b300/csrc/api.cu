@@ -252,6 +252,9 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   for (int k = 0; k < 10; ++k)
     LH_CUDA(c, cudaFuncSetAttribute(kerns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smems[k]));
   LH_CUDA(c, cudaFuncSetAttribute(o.k_remap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_remap));
+  LH_CUDA(c, cudaFuncSetAttribute(o.k_stiff_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)o.smem_stiff_setup));
+  LH_CUDA(c, cudaFuncSetAttribute(o.k_stiff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_stiff));
   c->grid_elem = (m.ne + o.nb - 1) / o.nb;
   int occ = 0;
   LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, o.k_cg, o.threads_cg, o.smem_cg));
@@ -295,6 +298,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {&c->ap, NV},                    {&c->a_prev, NV},            {&c->rhs, NV},
       {&c->xh, NV},                    {&c->vh, NV},                {&c->vb, NV},
       {&c->eh, NE * c->nl},            {&c->partials, npart},         {&c->zv, NV},
+      {&c->stiff_G, NE * (dim * (dim + 1) / 2) * NQ}, {&c->stiff_mq, NE * NQ}, {&c->stiff_inv, NV},
       {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
       {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
       {(double **)&c->ap32, nf * (NV + 1) / 2},       {(double **)&c->d32, nf * (NV + 1) / 2},
@@ -871,6 +875,63 @@ lh_status lh_remap_apply(lh_ctx *ctx, const double *x0, const double *x1, double
     if (lh_status st = check_launch(c, "remap mass gather")) return st;
   }
   return LH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stiffness operator and discrete Laplacian (Sections 2.1, 3.3, 6)
+// ---------------------------------------------------------------------------
+lh_status lh_stiffness_setup(lh_ctx *ctx, const double *x, lh_stream_t stream) {
+  if (!ctx || !x) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  lh_ctx *c = ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  StiffArgs a{};
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.x = x;
+  a.G = c->stiff_G;
+  a.mq = c->stiff_mq;
+  a.dvec = c->evec;   // [NE][ND] scratch, gathered below
+  a.status = c->dstatus;
+  c->ops->stiff_setup(a, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "stiffness setup")) return st;
+  c->ops->remap_nodes(c->mesh, nullptr, c->evec, 0, nullptr, c->stiff_inv, c->grid_node, kNodeThreads, s);
+  if (lh_status st = check_launch(c, "stiffness diagonal")) return st;
+  c->stiff_ready = true;
+  return LH_OK;
+}
+
+static lh_status stiff_apply(lh_ctx *c, const double *u, double *y, double scale, cudaStream_t s) {
+  StiffArgs a{};
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.G = c->stiff_G;
+  a.u = u;
+  a.evec = c->evec;
+  c->ops->stiff(a, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "stiffness action")) return st;
+  c->ops->gather(c->mesh, c->evec, c->dim, y, scale, nullptr, c->grid_node, kNodeThreads, s);
+  return check_launch(c, "stiffness gather");
+}
+
+lh_status lh_stiffness_mult(lh_ctx *ctx, const double *u, double *y, lh_stream_t stream) {
+  if (!ctx || !u || !y) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (u == y) return fail(ctx, LH_ERR_ARG, "u and y must not alias");
+  if (!ctx->stiff_ready) return fail(ctx, LH_ERR_ARG, "lh_stiffness_setup has not been called");
+  return stiff_apply(ctx, u, y, 1.0, (cudaStream_t)stream);
+}
+
+lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol, int max_it, lh_cg_info *info,
+                       lh_stream_t stream) {
+  if (!ctx || !v || !lap) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (v == lap) return fail(ctx, LH_ERR_ARG, "v and lap must not alias");
+  if (!ctx->stiff_ready) return fail(ctx, LH_ERR_ARG, "lh_stiffness_setup has not been called");
+  if (!(rel_tol == rel_tol)) return fail(ctx, LH_ERR_ARG, "bad tolerance");
+  if (rel_tol <= 0.0) rel_tol = 1e-12;
+  if (max_it <= 0) max_it = 1000;
+  lh_ctx *c = ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (lh_status st = stiff_apply(c, v, c->rhs, -1.0, s)) return st;   // rhs = -S v
+  return cg_impl(c, c->rhs, lap, rel_tol, max_it, info, nullptr, nullptr, s, c->stiff_mq, c->stiff_inv);
 }
 
 }  // extern "C"

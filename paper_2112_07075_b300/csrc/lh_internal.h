@@ -124,6 +124,19 @@ struct RemapArgs {
   int *status;
 };
 
+// Stiffness operator (Sections 2.1, 3.3): setup on a mesh and the PA action.
+struct StiffArgs {
+  MeshDesc mesh;
+  const double *tab;
+  const double *x;   // setup: H1 node positions [DIM][N_H1]
+  double *G;         // [NE][DIM(DIM+1)/2][NQ] PA data (setup writes, action reads)
+  double *mq;        // setup: out [NE][NQ] unit-density mass data omega det J
+  double *dvec;      // setup: out [NE][ND] element diagonal of that mass matrix
+  const double *u;   // action: input [DIM][N_H1]
+  double *evec;      // action: out [NE][DIM][ND]
+  int *status;
+};
+
 struct InitEArgs {
   MeshDesc mesh;
   const double *tab, *x0, *mq, *rho0, *me_inv;
@@ -168,6 +181,11 @@ struct Ops {
   void (*remap)(const RemapArgs &, int grid, cudaStream_t);
   void (*remap_nodes)(const MeshDesc &, const double *evec, const double *dvec, int constrained, double *rhs,
                       double *invdiag, int grid, int threads, cudaStream_t);
+  // stiffness operator: setup pass and action (element parts)
+  size_t smem_stiff_setup, smem_stiff;
+  void *k_stiff_setup, *k_stiff;
+  void (*stiff_setup)(const StiffArgs &, int grid, cudaStream_t);
+  void (*stiff)(const StiffArgs &, int grid, cudaStream_t);
 };
 
 const Ops *find_ops_2d(int p, int q1);
@@ -209,6 +227,10 @@ struct lh_ctx {
          *D = nullptr, *me_inv = nullptr, *invdiag = nullptr, *evec = nullptr, *r = nullptr, *pv = nullptr,
          *ap = nullptr, *a_prev = nullptr, *rhs = nullptr, *xh = nullptr, *vh = nullptr, *vb = nullptr,
          *eh = nullptr, *partials = nullptr, *zv = nullptr;
+  // stiffness operator on a mesh set by lh_stiffness_setup: PA data, unit-density mass
+  // data and its Jacobi inverse (every DOF)
+  double *stiff_G = nullptr, *stiff_mq = nullptr, *stiff_inv = nullptr;
+  bool stiff_ready = false;
   float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
         *evec32 = nullptr;
   int grid_cg_ir = 0, grid_cg_tc = 0;

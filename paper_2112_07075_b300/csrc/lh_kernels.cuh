@@ -1386,6 +1386,115 @@ struct Family {
     }
   }
 
+  // Adjugate A = adj(J) = det(J) J^-1 (row-major, A[l][c]) and det J at qpoint q of
+  // element b from reference gradients g[l][b*DIM + c][q] = dx_c/dxi_l (C = CX).
+  static __device__ __forceinline__ void adjugate(const double *g, int b, int q, double *A, double &det) {
+    double J[DIM * DIM];   // J[c][l] = dx_c/dxi_l
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) J[c * DIM + l] = g[(l * CX + b * DIM + c) * NQ + q];
+    if constexpr (DIM == 2) {
+      A[0] = J[3]; A[1] = -J[1]; A[2] = -J[2]; A[3] = J[0];
+      det = J[0] * J[3] - J[1] * J[2];
+    } else {
+      A[0] = J[4] * J[8] - J[5] * J[7]; A[1] = J[2] * J[7] - J[1] * J[8]; A[2] = J[1] * J[5] - J[2] * J[4];
+      A[3] = J[5] * J[6] - J[3] * J[8]; A[4] = J[0] * J[8] - J[2] * J[6]; A[5] = J[2] * J[3] - J[0] * J[5];
+      A[6] = J[3] * J[7] - J[4] * J[6]; A[7] = J[1] * J[6] - J[0] * J[7]; A[8] = J[0] * J[4] - J[1] * J[3];
+      det = J[0] * A[0] + J[1] * A[3] + J[2] * A[6];
+    }
+  }
+
+  // ===== stiffness (diffusion) operator, S_ij = int grad w_i . grad w_j dx ==========
+  // (Sections 2.1, 3.3: the hyper-viscosity operator; Section 3.1 decomposition with
+  // the reference gradients as B and G below as the qpoint data D.)
+  static constexpr int NS = DIM * (DIM + 1) / 2;   // upper triangle of a symmetric d x d
+  // Setup on the mesh at node positions x: G = omega adj(J) adj(J)^T / det J
+  // (= omega det J J^-1 J^-T) as [NE][NS][NQ] with (l, m >= l) row by row, the
+  // unit-density mass data omega det J and the element diagonal of that mass matrix.
+  // smem: tab | xu[CX][ND] | S | g[DIM][CX][NQ] | mqs[NB][NQ] | y[NB][ND]
+  static constexpr int SS_S = max3(grad_scratch<DIM, D, Q>(CX), interp_scratch<DIM, Q, D>(NB), 0);
+  static constexpr size_t stiff_setup_smem() {
+    return sizeof(double) * (TAB + CX * ND + SS_S + DIM * CX * NQ + NB * NQ + NB * ND);
+  }
+  static __device__ __forceinline__ void body_stiff_setup(const StiffArgs &a, int e0) {
+    extern __shared__ double sm[];
+    double *st = sm, *xu = st + TAB, *S = xu + CX * ND, *g = S + SS_S, *mqs = g + DIM * CX * NQ, *y = mqs + NB * NQ;
+    const MeshDesc &m = a.mesh;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(xu, a.x, DIM, m, e0, nb);
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(xu, g, S, st + oB, st + oG);
+    for (int k = threadIdx.x; k < NB * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      double mq = 0.0;
+      if (b < nb) {
+        double A[DIM * DIM], det, w, iw;
+        adjugate(g, b, q, A, det);
+        if (!(det > 0.0)) latch_status(a.status, 4);
+        qweight(st, q, w, iw);
+        mq = w * det;
+        const double s = w / det;
+        double *Ge = a.G + (size_t)(e0 + b) * NS * NQ + q;
+        int r = 0;
+#pragma unroll
+        for (int l = 0; l < DIM; ++l)
+#pragma unroll
+          for (int n = l; n < DIM; ++n) {
+            double t = 0.0;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) t = fma(A[l * DIM + c], A[n * DIM + c], t);
+            Ge[(size_t)(r++) * NQ] = s * t;
+          }
+        a.mq[(size_t)(e0 + b) * NQ + q] = mq;
+      }
+      mqs[k] = mq;
+    }
+    __syncthreads();
+    interp<DIM, Q, D, NB>(mqs, y, S, st + oB2t);   // sum_q mq B_i(q)^2
+    for (int k = threadIdx.x; k < nb * ND; k += blockDim.x) a.dvec[(size_t)e0 * ND + k] = y[k];
+  }
+  // Action on the DIM components of an H1 field: y_e = sum_q ghat^T G(q) ghat u_e.
+  // smem: tab | u[CX][ND] | S | g[DIM][CX][NQ] | gs[NB][NS][NQ]
+  static constexpr int SM_S = grad_scratch<DIM, D, Q>(CX);
+  static constexpr size_t stiff_smem() {
+    return sizeof(double) * (TAB + CX * ND + SM_S + DIM * CX * NQ + NB * NS * NQ);
+  }
+  static __device__ __forceinline__ void body_stiff(const StiffArgs &a, int e0) {
+    extern __shared__ double sm[];
+    double *st = sm, *u = st + TAB, *S = u + CX * ND, *g = S + SM_S, *gs = g + DIM * CX * NQ;
+    const MeshDesc &m = a.mesh;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(u, a.u, DIM, m, e0, nb);
+    for (int k = threadIdx.x; k < NB * NS * NQ; k += blockDim.x)   // one contiguous block per CTA
+      gs[k] = k / (NS * NQ) < nb ? a.G[(size_t)e0 * NS * NQ + k] : 0.0;
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(u, g, S, st + oB, st + oG);
+    for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
+      const int q = k % NQ, bc = k / NQ, b = bc / DIM;
+      double gl[DIM], Gs[NS];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) gl[l] = g[(l * CX + bc) * NQ + q];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) Gs[r] = gs[(b * NS + r) * NQ + q];
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) {
+        double t = 0.0;
+#pragma unroll
+        for (int n = 0; n < DIM; ++n) {
+          const int lo = l < n ? l : n, hi = l < n ? n : l;
+          t = fma(Gs[lo * DIM - lo * (lo - 1) / 2 + (hi - lo)], gl[n], t);
+        }
+        g[(l * CX + bc) * NQ + q] = t;
+      }
+    }
+    __syncthreads();
+    grad_ref_t<DIM, D, Q, CX>(g, u, S, st + oBt, st + oGt);
+    for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = u[k];
+  }
+
   // ===== remap phase (Section 3.5): one stage on the mesh x(tau) = x0 + tau u ====
   // Per element and qpoint of x(tau): mq = omega detJ (the mass data of M(tau)) and
   // the advection data adv_l = omega detJ (J^-1 u)_l = omega (adj(J) u)_l, kept in
@@ -1428,20 +1537,8 @@ struct Family {
 #pragma unroll
       for (int l = 0; l < DIM; ++l) al[l] = 0.0;
       if (b < nb) {
-        double J[DIM * DIM], A[DIM * DIM], det;   // J[c][l] = dx_c/dxi_l, A = adj(J) = det J^-1
-#pragma unroll
-        for (int c = 0; c < DIM; ++c)
-#pragma unroll
-          for (int l = 0; l < DIM; ++l) J[c * DIM + l] = g[(l * CX + b * DIM + c) * NQ + q];
-        if constexpr (DIM == 2) {
-          A[0] = J[3]; A[1] = -J[1]; A[2] = -J[2]; A[3] = J[0];
-          det = J[0] * J[3] - J[1] * J[2];
-        } else {
-          A[0] = J[4] * J[8] - J[5] * J[7]; A[1] = J[2] * J[7] - J[1] * J[8]; A[2] = J[1] * J[5] - J[2] * J[4];
-          A[3] = J[5] * J[6] - J[3] * J[8]; A[4] = J[0] * J[8] - J[2] * J[6]; A[5] = J[2] * J[3] - J[0] * J[5];
-          A[6] = J[3] * J[7] - J[4] * J[6]; A[7] = J[1] * J[6] - J[0] * J[7]; A[8] = J[0] * J[4] - J[1] * J[3];
-          det = J[0] * A[0] + J[1] * A[3] + J[2] * A[6];
-        }
+        double A[DIM * DIM], det;
+        adjugate(g, b, q, A, det);
         if (!(det > 0.0)) latch_status(a.status, 4);
         double w, iw;
         qweight(st, q, w, iw);
@@ -1502,5 +1599,9 @@ template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_init_e(InitEArgs a) { Family<DIM, P, Q>::body_init_e(a); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_remap(RemapArgs a) { Family<DIM, P, Q>::body_remap(a, blockIdx.x * Family<DIM, P, Q>::NB); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_stiff_setup(StiffArgs a) { Family<DIM, P, Q>::body_stiff_setup(a, blockIdx.x * Family<DIM, P, Q>::NB); }
+template <int DIM, int P, int Q>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_stiff(StiffArgs a) { Family<DIM, P, Q>::body_stiff(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 
 }  // namespace lh

@@ -125,6 +125,12 @@ struct OpsBuilder {
                           double *invdiag, int grid, int threads, cudaStream_t s) {
     k_remap_nodes<DIM, P + 1><<<grid, threads, 0, s>>>(m, evec, dvec, constrained, rhs, invdiag);
   }
+  static void stiff_setup(const StiffArgs &a, int grid, cudaStream_t s) {
+    k_stiff_setup<DIM, P, Q><<<grid, F::THREADS, F::stiff_setup_smem(), s>>>(a);
+  }
+  static void stiff(const StiffArgs &a, int grid, cudaStream_t s) {
+    k_stiff<DIM, P, Q><<<grid, F::THREADS, F::stiff_smem(), s>>>(a);
+  }
   static const Ops *get() {
     static const Ops ops = {DIM, P, Q, F::NB, F::THREADS, F::NBC, F::TC,
                             F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
@@ -137,7 +143,9 @@ struct OpsBuilder {
                             tc_kernel(), tc_smem(), kTc ? 512 : 0, tc_img_bytes(),
                             kTc ? &cg_tc : nullptr, kTc ? &tc_image : nullptr,
                             tc_apply_kernel(), kTc ? &tc_apply : nullptr,
-                            F::remap_smem(), (void *)k_remap<DIM, P, Q>, &remap, &remap_nodes};
+                            F::remap_smem(), (void *)k_remap<DIM, P, Q>, &remap, &remap_nodes,
+                            F::stiff_setup_smem(), F::stiff_smem(), (void *)k_stiff_setup<DIM, P, Q>,
+                            (void *)k_stiff<DIM, P, Q>, &stiff_setup, &stiff};
     return &ops;
   }
 };

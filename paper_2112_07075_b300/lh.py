@@ -31,7 +31,7 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_sync_status",
             "lh_learn_attach",
             "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc",
-            "lh_remap_velocity", "lh_remap_apply"]
+            "lh_remap_velocity", "lh_remap_apply", "lh_stiffness_setup", "lh_stiffness_mult", "lh_laplacian"]
 
 
 class LhParams(ctypes.Structure):
@@ -114,6 +114,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mass_mult_tc": (I, [P, VP, VP, VP]),
         "lh_remap_velocity": (I, [P, VP, VP, VP, I, I, D, I, VP, VP]),
         "lh_remap_apply": (I, [P, VP, VP, D, VP, VP, VP, VP]),
+        "lh_stiffness_setup": (I, [P, VP, VP]),
+        "lh_stiffness_mult": (I, [P, VP, VP, VP]),
+        "lh_laplacian": (I, [P, VP, VP, D, I, VP, VP]),
         "lh_timing_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
@@ -290,6 +293,16 @@ class Context:
     def remap_apply(self, x0, x1, tau, v, kv=None, mv=None):
         self._check(self.lib.lh_remap_apply(self.h, _ptr(x0), _ptr(x1), float(tau), _ptr(v), _ptr(kv), _ptr(mv),
                                             _stream()))
+
+    def stiffness_setup(self, x):
+        self._check(self.lib.lh_stiffness_setup(self.h, _ptr(x), _stream()))
+
+    def stiffness_mult(self, u, y):
+        self._check(self.lib.lh_stiffness_mult(self.h, _ptr(u), _ptr(y), _stream()))
+
+    def laplacian(self, v, lap, rel_tol=1e-12, max_it=1000, info=None):
+        self._check(self.lib.lh_laplacian(self.h, _ptr(v), _ptr(lap), float(rel_tol), int(max_it), _ptr(info),
+                                          _stream()))
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))
