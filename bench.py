@@ -353,14 +353,16 @@ def run_ours(args):
     learned = None
     remap = None
     stiffness = None
+    tmop = None
     if not args.no_forms and world == 1:
-        which = ("precision", "batching", "learned", "remap", "stiffness") if args.forms == "all" \
+        which = ("precision", "batching", "learned", "remap", "stiffness", "tmop") if args.forms == "all" \
             else (args.forms,)
         forms = forms_report(flush) if "precision" in which else None
         batching = batching_report(flush) if "batching" in which else None
         learned = learned_report(flush) if "learned" in which else None
         remap = remap_report(flush) if "remap" in which else None
         stiffness = stiffness_report(flush) if "stiffness" in which else None
+        tmop = tmop_report(flush) if "tmop" in which else None
     clk.__exit__()
     clocks = clk.summary()
     clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
@@ -385,6 +387,7 @@ def run_ours(args):
             "forms": {"precision": forms, "batching": batching, "learned": learned},
             "remap": remap,
             "stiffness": stiffness,
+            "tmop": tmop,
             "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
             "device_status": status, "wall_s_timed": wall,
         }
@@ -804,6 +807,67 @@ def stiffness_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
     }
 
 
+def tmop_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
+    """TMOP kernels (Section 2.2, Section 3.4 Eqs. 6-7, Jacobi diagonal) on the
+    Lagrangian mesh of the headline workload after `lagrange_steps` CFL steps, with the
+    initial mesh as x0 of the limiting term: target W = h I, h = 1/n, gamma = 0.1,
+    d = h/2. Events around each call (element pass + gather), L2 flushed, median of 5."""
+    import torch
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context
+    wl = WORKLOADS[wl_name]
+    dim, n, p, q1 = wl["dim"], wl["n"], wl["order"], wl["q1"]
+    V = inputs.box_vertices(dim, n, jitter=wl["jitter"], seed=3)
+    ctx = Context(dim, n, V, p, q1, cfl=wl["cfl"])
+    x, v, e = ctx.init_state("taylor_green")
+    x_init = x.clone()
+    info = ctx.new_step_info(0.0, wl["t_end"])
+    for _ in range(lagrange_steps):
+        ctx.rk2avg_step(x, v, e, 0.0, info)
+    stream = torch.cuda.current_stream()
+    kw = dict(h=1.0 / n, gamma=0.1, dlim=0.5 / n)
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g, y, dg = ctx.h1_vector(), ctx.h1_vector(), ctx.h1_vector()
+    u = ctx.h1_vector()
+    u.copy_(v)
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            flush.fill_(9.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[1:])
+
+    t = {"objective": timed(lambda: ctx.tmop_objective(x, x_init, F, **kw)),
+         "gradient": timed(lambda: ctx.tmop_gradient(x, x_init, g, **kw)),
+         "hessian_mult": timed(lambda: ctx.tmop_hessian_mult(x, u, y, **kw)),
+         "hessian_diag": timed(lambda: ctx.tmop_hessian_diag(x, dg, **kw))}
+    st = ctx.sync_status()
+    sz = ctx.sizes
+    D, Q = p + 1, q1
+    grad = 2 * Q * D ** 3 + 3 * Q * Q * D * D + 3 * Q ** 3 * D if dim == 3 else 2 * Q * D * D + 2 * Q * Q * D
+    interp = Q * D ** 3 + Q * Q * D * D + Q ** 3 * D if dim == 3 else Q * D * D + Q * Q * D
+    npair = dim * (dim + 1) // 2
+    # contraction FMAs per element (the pointwise metric work comes on top)
+    fma = {"objective": dim * (grad + interp), "gradient": dim * (2 * grad + 2 * interp),
+           "hessian_mult": dim * (3 * grad + 2 * interp), "hessian_diag": dim * grad + (npair * dim + 1) * interp}
+    out = {"workload": f"{wl['desc']}; Lagrangian mesh after {lagrange_steps} CFL steps, x0 = the initial mesh",
+           "params": kw, "objective_value": float(F.item()), "status": st}
+    for k, ms in t.items():
+        out[k] = {"ms": ms, "contraction_gflop": 2 * sz.ne * fma[k] / 1e9,
+                  "contraction_tflops": 2 * sz.ne * fma[k] / (ms * 1e-3) / 1e12}
+    out["note"] = ("events around each call (fully matrix-free element pass with the metric and its "
+                   "derivatives at every qpoint, plus the node gather for the vectors); contraction FLOPs "
+                   "only, the pointwise metric work is extra")
+    ctx.close()
+    return out
+
+
 def remap_cpu_baseline(n=12):
     """The oracle's remap (global assembly, direct solves) on one pseudo-time step of
     an n^3 Q2 mesh with a smooth displacement (a bounded sample: LU of the 3D mass
@@ -896,7 +960,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--forms", default="all",
-                    choices=["all", "precision", "batching", "learned", "remap", "stiffness"],
+                    choices=["all", "precision", "batching", "learned", "remap", "stiffness", "tmop"],
                     help="which form reports to add (default all; --no-forms for none)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "bf16tc_ir"],
                     help="mass-solve precision of the main arm (the headline workload is FP64)")

@@ -320,6 +320,44 @@ lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol
                        lh_cg_info *info, lh_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Mesh optimisation kernels (TMOP; Section 2.2 objective, Section 3.4 Eqs. 6-7).
+ *
+ * F(x) = int mu(T(x)) + gamma int |x - x0|^2 / d^2 over the target elements
+ * (quadrature weights w_q det W), T = A W^-1 with A = dx/dxbar on the reference
+ * element [0,1]^dim and the target W = h I (the ideal element of size h). Metric:
+ * mu_2(T) = |T|^2 / (2 det T) - 1 in 2D, mu_303(T) = |T|^2 / (3 det(T)^(2/3)) - 1 in
+ * 3D (shape metrics, zero on scaled rotations). Fully matrix-free: the metric and
+ * its first and second derivatives are evaluated at each quadrature point inside
+ * one sum-factorized element pass per call; vectors are gathered deterministically.
+ * An element with det T <= 0 latches LH_ERR_INVERTED in the context status.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double target_size;  /* h of W = h I (> 0) */
+  double lim_weight;   /* gamma (>= 0; 0 switches the limiting term off) */
+  double lim_dist;     /* d, the constant displacement limit (> 0 when gamma > 0) */
+} lh_tmop_params;
+
+/* F(x) -> *F (DEVICE double). x, x0: DEVICE [dim][N_H1]; x0 may be NULL when
+ * gamma = 0. Deterministic (fixed-order block sums). */
+lh_status lh_tmop_objective(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, const double *x0,
+                            double *F, lh_stream_t stream);
+
+/* g = dF/dx (Eq. 6 plus the limiting term), DEVICE [dim][N_H1], no boundary
+ * conditions; g must not alias x or x0. */
+lh_status lh_tmop_gradient(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, const double *x0,
+                           double *g, lh_stream_t stream);
+
+/* y = (d^2F/dx^2) u (Eq. 7 plus the limiting term) at x; x, u, y DEVICE
+ * [dim][N_H1]; y must not alias x or u. */
+lh_status lh_tmop_hessian_mult(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, const double *u,
+                               double *y, lh_stream_t stream);
+
+/* diag = the diagonal of d^2F/dx^2 at x (the Jacobi preconditioner of the Newton
+ * solve), DEVICE [dim][N_H1]; must not alias x. */
+lh_status lh_tmop_hessian_diag(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, double *diag,
+                               lh_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Batching form: many independent problems advanced together.
  *
  * A batch references existing contexts (2D, q1 = 2*order, LH_PRECISION_FP64;

@@ -255,6 +255,8 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   LH_CUDA(c, cudaFuncSetAttribute(o.k_stiff_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)o.smem_stiff_setup));
   LH_CUDA(c, cudaFuncSetAttribute(o.k_stiff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_stiff));
+  for (int k = 0; k < 4; ++k)
+    LH_CUDA(c, cudaFuncSetAttribute(o.k_tmop[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_tmop[k]));
   c->grid_elem = (m.ne + o.nb - 1) / o.nb;
   int occ = 0;
   LH_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, o.k_cg, o.threads_cg, o.smem_cg));
@@ -932,6 +934,77 @@ lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol
   cudaStream_t s = (cudaStream_t)stream;
   if (lh_status st = stiff_apply(c, v, c->rhs, -1.0, s)) return st;   // rhs = -S v
   return cg_impl(c, c->rhs, lap, rel_tol, max_it, info, nullptr, nullptr, s, c->stiff_mq, c->stiff_inv);
+}
+
+// ---------------------------------------------------------------------------
+// Mesh optimisation (TMOP, Sections 2.2 and 3.4)
+// ---------------------------------------------------------------------------
+static lh_status tmop_args(lh_ctx *c, const lh_tmop_params *prm, const double *x, TmopArgs &a) {
+  if (!prm || !x) return fail(c, LH_ERR_ARG, "null pointer");
+  if (!(prm->target_size > 0.0)) return fail(c, LH_ERR_ARG, "target_size must be > 0");
+  if (!(prm->lim_weight >= 0.0)) return fail(c, LH_ERR_ARG, "lim_weight must be >= 0");
+  if (prm->lim_weight > 0.0 && !(prm->lim_dist > 0.0)) return fail(c, LH_ERR_ARG, "lim_dist must be > 0");
+  a = TmopArgs{};
+  a.mesh = c->mesh;
+  a.tab = c->tab;
+  a.x = x;
+  a.h_inv = 1.0 / prm->target_size;
+  a.detW = std::pow(prm->target_size, (double)c->dim);
+  a.lim = prm->lim_weight > 0.0 ? prm->lim_weight / (prm->lim_dist * prm->lim_dist) : 0.0;
+  a.evec = c->evec;
+  a.status = c->dstatus;
+  return LH_OK;
+}
+
+static lh_status tmop_vector(lh_ctx *c, int mode, const TmopArgs &a, double *out, cudaStream_t s) {
+  c->ops->tmop(mode, a, c->grid_elem, s);
+  if (lh_status st = check_launch(c, "tmop element pass")) return st;
+  c->ops->gather(c->mesh, c->evec, c->dim, out, 1.0, nullptr, c->grid_node, kNodeThreads, s);
+  return check_launch(c, "tmop gather");
+}
+
+lh_status lh_tmop_objective(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, const double *x0, double *F,
+                            lh_stream_t stream) {
+  if (!ctx || !F) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  TmopArgs a;
+  if (lh_status st = tmop_args(ctx, prm, x, a)) return st;
+  if (a.lim != 0.0 && !x0) return fail(ctx, LH_ERR_ARG, "x0 is required with a limiting term");
+  a.x0 = x0;
+  a.partials = ctx->partials;
+  a.counter = ctx->counter;
+  a.out = F;
+  ctx->ops->tmop(0, a, ctx->grid_elem, (cudaStream_t)stream);
+  return check_launch(ctx, "tmop objective");
+}
+
+lh_status lh_tmop_gradient(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, const double *x0, double *g,
+                           lh_stream_t stream) {
+  if (!ctx || !g) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  TmopArgs a;
+  if (lh_status st = tmop_args(ctx, prm, x, a)) return st;
+  if (a.lim != 0.0 && !x0) return fail(ctx, LH_ERR_ARG, "x0 is required with a limiting term");
+  if (g == x || g == x0) return fail(ctx, LH_ERR_ARG, "g must not alias x or x0");
+  a.x0 = x0;
+  return tmop_vector(ctx, 1, a, g, (cudaStream_t)stream);
+}
+
+lh_status lh_tmop_hessian_mult(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, const double *u, double *y,
+                               lh_stream_t stream) {
+  if (!ctx || !u || !y) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  TmopArgs a;
+  if (lh_status st = tmop_args(ctx, prm, x, a)) return st;
+  if (y == x || y == u) return fail(ctx, LH_ERR_ARG, "y must not alias x or u");
+  a.u = u;
+  return tmop_vector(ctx, 2, a, y, (cudaStream_t)stream);
+}
+
+lh_status lh_tmop_hessian_diag(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, double *diag,
+                               lh_stream_t stream) {
+  if (!ctx || !diag) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  TmopArgs a;
+  if (lh_status st = tmop_args(ctx, prm, x, a)) return st;
+  if (diag == x) return fail(ctx, LH_ERR_ARG, "diag must not alias x");
+  return tmop_vector(ctx, 3, a, diag, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -137,6 +137,22 @@ struct StiffArgs {
   int *status;
 };
 
+// Mesh optimisation (TMOP, Sections 2.2 and 3.4): one fully matrix-free element pass.
+struct TmopArgs {
+  MeshDesc mesh;
+  const double *tab;
+  const double *x;     // positions [DIM][N_H1]
+  const double *x0;    // limiting reference positions (objective, gradient), or NULL
+  const double *u;     // Hessian action: direction [DIM][N_H1]
+  double h_inv, detW;  // target W = h I: 1/h, h^DIM
+  double lim;          // gamma / d^2 (0: no limiting term)
+  double *evec;        // gradient / Hessian action / diagonal: [NE][DIM][ND]
+  double *partials;    // objective: block sums, last-block total into *out
+  unsigned int *counter;
+  double *out;
+  int *status;
+};
+
 struct InitEArgs {
   MeshDesc mesh;
   const double *tab, *x0, *mq, *rho0, *me_inv;
@@ -186,6 +202,10 @@ struct Ops {
   void *k_stiff_setup, *k_stiff;
   void (*stiff_setup)(const StiffArgs &, int grid, cudaStream_t);
   void (*stiff)(const StiffArgs &, int grid, cudaStream_t);
+  // TMOP element passes, mode 0 objective, 1 gradient, 2 Hessian action, 3 diagonal
+  size_t smem_tmop[4];
+  void *k_tmop[4];
+  void (*tmop)(int mode, const TmopArgs &, int grid, cudaStream_t);
 };
 
 const Ops *find_ops_2d(int p, int q1);

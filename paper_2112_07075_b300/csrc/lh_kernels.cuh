@@ -1495,6 +1495,291 @@ struct Family {
     for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = u[k];
   }
 
+  // ===== mesh optimisation (TMOP, Sections 2.2 and 3.4), fully matrix-free =======
+  // Target W = h I (W^-1 = I/h, det W = h^d), T = A W^-1 with A = dx/dxbar; shape
+  // metrics mu_2 = |T|^2/(2 det T) - 1 (2D) and mu_303 = |T|^2/(3 det T^(2/3)) - 1 (3D);
+  // limiting term lim * |x - x0|^2 (lim = gamma/d^2), both integrated with w_q det W.
+  // Every quantity at the qpoints is computed on the fly (no stored qpoint data).
+  enum { TM_OBJ = 0, TM_GRAD = 1, TM_HESS = 2, TM_DIAG = 3 };
+  static constexpr int NPAIR = NS;   // (n, p >= n) pairs of the diagonal blocks
+
+  // Cofactor C = d(det T)/dT (row-major) and det T.
+  static __device__ __forceinline__ double cofactor(const double *T, double *C) {
+    if constexpr (DIM == 2) {
+      C[0] = T[3]; C[1] = -T[2]; C[2] = -T[1]; C[3] = T[0];
+      return T[0] * T[3] - T[1] * T[2];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {   // row a of C = row b x row c, (a, b, c) cyclic
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        C[a * 3 + 0] = T[b * 3 + 1] * T[c * 3 + 2] - T[b * 3 + 2] * T[c * 3 + 1];
+        C[a * 3 + 1] = T[b * 3 + 2] * T[c * 3 + 0] - T[b * 3 + 0] * T[c * 3 + 2];
+        C[a * 3 + 2] = T[b * 3 + 0] * T[c * 3 + 1] - T[b * 3 + 1] * T[c * 3 + 0];
+      }
+      return T[0] * C[0] + T[1] * C[1] + T[2] * C[2];
+    }
+  }
+  // Scalar factors of the metric and its derivatives at one T:
+  //   mu, dmu = cT T + cC C,
+  //   d2mu[Z] = cZ Z + cTC ((C:Z) T + (T:Z) C) + cCC (C:Z) C + cdC dC[Z].
+  struct MetricCoef {
+    double mu, cT, cC, cZ, cTC, cCC, cdC;
+  };
+  static __device__ __forceinline__ MetricCoef metric(double n2, double tau) {
+    MetricCoef k;
+    if constexpr (DIM == 2) {
+      const double it = 1.0 / tau;
+      k.mu = 0.5 * n2 * it - 1.0;
+      k.cT = it;
+      k.cC = -0.5 * n2 * it * it;
+      k.cZ = it;
+      k.cTC = -it * it;
+      k.cCC = n2 * it * it * it;
+      k.cdC = -0.5 * n2 * it * it;
+    } else {
+      const double c13 = cbrt(tau);
+      const double r = 1.0 / (c13 * c13);   // tau^(-2/3)
+      const double it = 1.0 / tau;
+      k.mu = n2 * r * (1.0 / 3.0) - 1.0;
+      k.cT = (2.0 / 3.0) * r;
+      k.cC = -(2.0 / 9.0) * n2 * r * it;
+      k.cZ = (2.0 / 3.0) * r;
+      k.cTC = -(4.0 / 9.0) * r * it;
+      k.cCC = (10.0 / 27.0) * n2 * r * it * it;
+      k.cdC = -(2.0 / 9.0) * n2 * r * it;
+    }
+    return k;
+  }
+  // dC[Z] = d/de cof(T + e Z) at e = 0.
+  static __device__ __forceinline__ void dcofactor(const double *T, const double *Z, double *dC) {
+    if constexpr (DIM == 2) {
+      dC[0] = Z[3]; dC[1] = -Z[2]; dC[2] = -Z[1]; dC[3] = Z[0];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {   // row a: Z_b x T_c + T_b x Z_c
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+          dC[a * 3 + j] = Z[b * 3 + j1] * T[c * 3 + j2] - Z[b * 3 + j2] * T[c * 3 + j1] +
+                          T[b * 3 + j1] * Z[c * 3 + j2] - T[b * 3 + j2] * Z[c * 3 + j1];
+        }
+      }
+    }
+  }
+  // Per-axis-table contraction from the qpoints to the nodes (Q -> D on every axis,
+  // tables [D][Q]): out[c][iz][iy][ix] = sum Mx[ix][qx] My[iy][qy] Mz[iz][qz] in[c][qz][qy][qx].
+  template <int C>
+  static __device__ __forceinline__ void interp_axes_t(const double *in, double *out, double *S, const double *Mx,
+                                                       const double *My, const double *Mz) {
+    if constexpr (DIM == 2) {
+      contract<C * Q, Q, D, 1>(in, S, Mx);
+      __syncthreads();
+      contract<C, Q, D, D>(S, out, My);
+      __syncthreads();
+    } else {
+      double *t2 = S + C * Q * Q * D;
+      contract<C * Q * Q, Q, D, 1>(in, S, Mx);
+      __syncthreads();
+      contract<C * Q, Q, D, D>(S, t2, My);
+      __syncthreads();
+      contract<C, Q, D, D * D>(t2, out, Mz);
+      __syncthreads();
+    }
+  }
+  // smem per mode (doubles):
+  //   OBJ/GRAD: tab | xu[CX][ND] | du[CX][ND] | S | g[DIM][CX][NQ] | dq[CX][NQ] | red
+  //   HESS:     tab | xu | uu | S | g[DIM][CX][NQ] | gu[DIM][CX][NQ] | uq[CX][NQ]
+  //   DIAG:     tab | xu | y[CX][ND] | S | g[DIM][CX][NQ] | cq[NPAIR][CX][NQ] | mq[NB][NQ] | G2t | GBt
+  static constexpr int TM_S = max3(grad_scratch<DIM, D, Q>(CX), interp_scratch<DIM, D, Q>(CX),
+                                   interp_scratch<DIM, Q, D>(CX));
+  static constexpr int TQD = ((2 * D * Q) + 1) / 2 * 2;
+  static constexpr size_t tmop_smem(int mode) {
+    return sizeof(double) *
+           (mode == TM_HESS ? TAB + 2 * CX * ND + TM_S + 2 * DIM * CX * NQ + CX * NQ
+            : mode == TM_DIAG ? TAB + 2 * CX * ND + TM_S + DIM * CX * NQ + NPAIR * CX * NQ + NB * NQ + TQD
+                              : TAB + 2 * CX * ND + TM_S + DIM * CX * NQ + CX * NQ + RED);
+  }
+  template <int MODE>
+  static __device__ __forceinline__ void body_tmop(const TmopArgs &a, int e0) {
+    extern __shared__ double sm[];
+    double *st = sm, *xu = st + TAB, *uu = xu + CX * ND, *S = uu + CX * ND, *g = S + TM_S;
+    double *q1 = g + DIM * CX * NQ;   // OBJ/GRAD: dq; HESS: gu; DIAG: cq
+    const MeshDesc &m = a.mesh;
+    const int nb = min(NB, m.ne - e0);
+    const bool lim = a.lim != 0.0 && (MODE == TM_HESS || MODE == TM_DIAG || a.x0 != nullptr);
+    load_tab(st, a.tab);
+    for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+      const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+      double x = 0.0, w = 0.0;
+      if (b < nb) {
+        const size_t gi = (size_t)c * m.nh1 + h1_node<DIM, D>(m, e0 + b, i);
+        x = a.x[gi];
+        if (MODE == TM_HESS) w = a.u[gi];
+        else if ((MODE == TM_OBJ || MODE == TM_GRAD) && lim) w = x - a.x0[gi];
+      }
+      xu[k] = x;
+      if (MODE != TM_DIAG) uu[k] = w;
+    }
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(xu, g, S, st + oB, st + oG);   // A = dx/dxbar
+    if (MODE == TM_HESS) {
+      grad_ref<DIM, D, Q, CX>(uu, q1, S, st + oB, st + oG);   // du/dxbar
+      if (lim) interp<DIM, D, Q, CX>(uu, q1 + DIM * CX * NQ, S, st + oB);
+    } else if (MODE != TM_DIAG && lim) {
+      interp<DIM, D, Q, CX>(uu, q1, S, st + oB);   // x - x0 at the qpoints
+    }
+    const double hi = a.h_inv, wdet = a.detW;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < NB * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      if (b >= nb) {
+        if (MODE == TM_DIAG)
+          for (int r = 0; r < NPAIR * DIM; ++r) q1[(r / DIM * CX + b * DIM + r % DIM) * NQ + q] = 0.0;
+        if (MODE == TM_DIAG) q1[NPAIR * CX * NQ + k] = 0.0;
+        continue;
+      }
+      double Tm[DIM * DIM], C[DIM * DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) Tm[c * DIM + l] = hi * g[(l * CX + b * DIM + c) * NQ + q];
+      const double tau = cofactor(Tm, C);
+      if (!(tau > 0.0)) latch_status(a.status, 4);
+      double n2 = 0.0;
+#pragma unroll
+      for (int r = 0; r < DIM * DIM; ++r) n2 = fma(Tm[r], Tm[r], n2);
+      const MetricCoef mc = metric(n2, tau);
+      double w, iw;
+      qweight(st, q, w, iw);
+      const double wq = w * wdet;
+      if (MODE == TM_OBJ) {
+        double s = mc.mu;
+        if (lim) {
+          double d2 = 0.0;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            const double dv = q1[(b * DIM + c) * NQ + q];
+            d2 = fma(dv, dv, d2);
+          }
+          s = fma(a.lim, d2, s);
+        }
+        acc = fma(wq, s, acc);
+      } else if (MODE == TM_GRAD) {
+        const double f = wq * hi;   // f[n][a] = w detW / h * dmu_an
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int n = 0; n < DIM; ++n)
+            g[(n * CX + b * DIM + c) * NQ + q] = f * fma(mc.cT, Tm[c * DIM + n], mc.cC * C[c * DIM + n]);
+        if (lim)
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) q1[(b * DIM + c) * NQ + q] *= 2.0 * a.lim * wq;
+      } else if (MODE == TM_HESS) {
+        double Z[DIM * DIM], dC[DIM * DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int l = 0; l < DIM; ++l) Z[c * DIM + l] = hi * q1[(l * CX + b * DIM + c) * NQ + q];
+        dcofactor(Tm, Z, dC);
+        double cz = 0.0, tz = 0.0;
+#pragma unroll
+        for (int r = 0; r < DIM * DIM; ++r) {
+          cz = fma(C[r], Z[r], cz);
+          tz = fma(Tm[r], Z[r], tz);
+        }
+        const double f = wq * hi;
+        const double kT = mc.cTC * cz, kC = fma(mc.cTC, tz, mc.cCC * cz);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int n = 0; n < DIM; ++n) {
+            const int r = c * DIM + n;
+            const double v = fma(mc.cZ, Z[r], fma(kT, Tm[r], fma(kC, C[r], mc.cdC * dC[r])));
+            g[(n * CX + b * DIM + c) * NQ + q] = f * v;
+          }
+        if (lim)
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) q1[DIM * CX * NQ + (b * DIM + c) * NQ + q] *= 2.0 * a.lim * wq;
+      } else {   // TM_DIAG: H_a[n][p] = cZ d_np + cTC (C_ap T_an + T_ap C_an) + cCC C_an C_ap
+        const double f = wq * hi * hi;
+        int r = 0;
+#pragma unroll
+        for (int n = 0; n < DIM; ++n)
+#pragma unroll
+          for (int p = n; p < DIM; ++p, ++r) {
+            const double sym = n == p ? 1.0 : 2.0;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+              const double Can = C[c * DIM + n], Cap = C[c * DIM + p];
+              const double Tan = Tm[c * DIM + n], Tap = Tm[c * DIM + p];
+              double hv = mc.cTC * fma(Cap, Tan, Tap * Can) + mc.cCC * Can * Cap;
+              if (n == p) hv += mc.cZ;
+              q1[(r * CX + b * DIM + c) * NQ + q] = sym * f * hv;
+            }
+          }
+        q1[NPAIR * CX * NQ + k] = lim ? 2.0 * a.lim * wq : 0.0;
+      }
+    }
+    if (MODE == TM_OBJ) {
+      double v1[1] = {acc};
+      bsum<1>(v1, q1 + CX * NQ);
+      __shared__ int s_last;
+      if (threadIdx.x == 0) {
+        a.partials[blockIdx.x] = v1[0];
+        __threadfence();
+        s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+      }
+      __syncthreads();
+      if (!s_last || threadIdx.x >= 32) return;
+      __threadfence();
+      double sacc = 0.0;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) sacc += ((volatile double *)a.partials)[i];
+      sacc = warp_sum(sacc);
+      if (threadIdx.x == 0) {
+        *a.counter = 0u;
+        *a.out = sacc;
+      }
+      return;
+    }
+    __syncthreads();
+    if (MODE == TM_GRAD || MODE == TM_HESS) {
+      grad_ref_t<DIM, D, Q, CX>(g, xu, S, st + oBt, st + oGt);   // sum_q sum_n dw_i/dxbar_n f[n][c]
+      const double *lq = MODE == TM_HESS ? q1 + DIM * CX * NQ : q1;
+      if (lim) interp<DIM, Q, D, CX>(lq, uu, S, st + oBt);        // sum_q w_i (limiting factor)
+      for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x)
+        a.evec[(size_t)e0 * DIM * ND + k] = lim ? xu[k] + uu[k] : xu[k];
+      return;
+    }
+    // TM_DIAG: sum over pairs of per-axis contractions with the tables G^2, G B, B^2
+    double *G2t = q1 + NPAIR * CX * NQ + NB * NQ, *GBt = G2t + D * Q;
+    for (int k = threadIdx.x; k < D * Q; k += blockDim.x) {
+      const double gt = st[oGt + k], bt = st[oBt + k];
+      G2t[k] = gt * gt;
+      GBt[k] = gt * bt;
+    }
+    __syncthreads();
+    double *y = uu;
+    for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) xu[k] = 0.0;
+    int r = 0;
+    for (int n = 0; n < DIM; ++n)
+      for (int p = n; p < DIM; ++p, ++r) {
+        const double *M[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+          M[ax] = (ax == n && ax == p) ? G2t : (ax == n || ax == p) ? GBt : st + oB2t;
+        interp_axes_t<CX>(q1 + r * CX * NQ, y, S, M[0], M[1], M[2]);
+        for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) xu[k] += y[k];
+        __syncthreads();
+      }
+    if (lim) {
+      interp<DIM, Q, D, NB>(q1 + NPAIR * CX * NQ, y, S, st + oB2t);   // 2 lim w detW w_i^2
+      for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) xu[k] += y[(k / (DIM * ND)) * ND + k % ND];
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = xu[k];
+  }
+
   // ===== remap phase (Section 3.5): one stage on the mesh x(tau) = x0 + tau u ====
   // Per element and qpoint of x(tau): mq = omega detJ (the mass data of M(tau)) and
   // the advection data adv_l = omega detJ (J^-1 u)_l = omega (adj(J) u)_l, kept in
@@ -1603,5 +1888,7 @@ template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_stiff_setup(StiffArgs a) { Family<DIM, P, Q>::body_stiff_setup(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_stiff(StiffArgs a) { Family<DIM, P, Q>::body_stiff(a, blockIdx.x * Family<DIM, P, Q>::NB); }
+template <int DIM, int P, int Q, int MODE>
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_tmop(TmopArgs a) { Family<DIM, P, Q>::template body_tmop<MODE>(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 
 }  // namespace lh

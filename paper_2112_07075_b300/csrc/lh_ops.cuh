@@ -131,6 +131,14 @@ struct OpsBuilder {
   static void stiff(const StiffArgs &a, int grid, cudaStream_t s) {
     k_stiff<DIM, P, Q><<<grid, F::THREADS, F::stiff_smem(), s>>>(a);
   }
+  static void tmop(int mode, const TmopArgs &a, int grid, cudaStream_t s) {
+    switch (mode) {
+      case 0: k_tmop<DIM, P, Q, 0><<<grid, F::THREADS, F::tmop_smem(0), s>>>(a); break;
+      case 1: k_tmop<DIM, P, Q, 1><<<grid, F::THREADS, F::tmop_smem(1), s>>>(a); break;
+      case 2: k_tmop<DIM, P, Q, 2><<<grid, F::THREADS, F::tmop_smem(2), s>>>(a); break;
+      default: k_tmop<DIM, P, Q, 3><<<grid, F::THREADS, F::tmop_smem(3), s>>>(a); break;
+    }
+  }
   static const Ops *get() {
     static const Ops ops = {DIM, P, Q, F::NB, F::THREADS, F::NBC, F::TC,
                             F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
@@ -145,7 +153,11 @@ struct OpsBuilder {
                             tc_apply_kernel(), kTc ? &tc_apply : nullptr,
                             F::remap_smem(), (void *)k_remap<DIM, P, Q>, &remap, &remap_nodes,
                             F::stiff_setup_smem(), F::stiff_smem(), (void *)k_stiff_setup<DIM, P, Q>,
-                            (void *)k_stiff<DIM, P, Q>, &stiff_setup, &stiff};
+                            (void *)k_stiff<DIM, P, Q>, &stiff_setup, &stiff,
+                            {F::tmop_smem(0), F::tmop_smem(1), F::tmop_smem(2), F::tmop_smem(3)},
+                            {(void *)k_tmop<DIM, P, Q, 0>, (void *)k_tmop<DIM, P, Q, 1>, (void *)k_tmop<DIM, P, Q, 2>,
+                             (void *)k_tmop<DIM, P, Q, 3>},
+                            &tmop};
     return &ops;
   }
 };

@@ -31,7 +31,8 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_sync_status",
             "lh_learn_attach",
             "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc",
-            "lh_remap_velocity", "lh_remap_apply", "lh_stiffness_setup", "lh_stiffness_mult", "lh_laplacian"]
+            "lh_remap_velocity", "lh_remap_apply", "lh_stiffness_setup", "lh_stiffness_mult", "lh_laplacian",
+            "lh_tmop_objective", "lh_tmop_gradient", "lh_tmop_hessian_mult", "lh_tmop_hessian_diag"]
 
 
 class LhParams(ctypes.Structure):
@@ -56,6 +57,10 @@ class LhStepInfo(ctypes.Structure):
                 ("dt_est", ctypes.c_double), ("energy_src", ctypes.c_double),
                 ("cg_rel_res", ctypes.c_double * 2), ("cg_iters", ctypes.c_int * 2),
                 ("status", ctypes.c_int), ("steps", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong)]
+
+
+class LhTmopParams(ctypes.Structure):
+    _fields_ = [("target_size", ctypes.c_double), ("lim_weight", ctypes.c_double), ("lim_dist", ctypes.c_double)]
 
 
 class LhRemapInfo(ctypes.Structure):
@@ -117,6 +122,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_stiffness_setup": (I, [P, VP, VP]),
         "lh_stiffness_mult": (I, [P, VP, VP, VP]),
         "lh_laplacian": (I, [P, VP, VP, D, I, VP, VP]),
+        "lh_tmop_objective": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP, VP]),
+        "lh_tmop_gradient": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP, VP]),
+        "lh_tmop_hessian_mult": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP, VP]),
+        "lh_tmop_hessian_diag": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP]),
         "lh_timing_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
@@ -303,6 +312,27 @@ class Context:
     def laplacian(self, v, lap, rel_tol=1e-12, max_it=1000, info=None):
         self._check(self.lib.lh_laplacian(self.h, _ptr(v), _ptr(lap), float(rel_tol), int(max_it), _ptr(info),
                                           _stream()))
+
+    @staticmethod
+    def _tmop_prm(h, gamma, dlim):
+        return ctypes.byref(LhTmopParams(float(h), float(gamma), float(dlim)))
+
+    def tmop_objective(self, x, x0, out, h, gamma=0.0, dlim=1.0):
+        """F(x) into the DEVICE float64 tensor `out` (one element)."""
+        self._check(self.lib.lh_tmop_objective(self.h, self._tmop_prm(h, gamma, dlim), _ptr(x), _ptr(x0),
+                                               _ptr(out), _stream()))
+
+    def tmop_gradient(self, x, x0, g, h, gamma=0.0, dlim=1.0):
+        self._check(self.lib.lh_tmop_gradient(self.h, self._tmop_prm(h, gamma, dlim), _ptr(x), _ptr(x0), _ptr(g),
+                                              _stream()))
+
+    def tmop_hessian_mult(self, x, u, y, h, gamma=0.0, dlim=1.0):
+        self._check(self.lib.lh_tmop_hessian_mult(self.h, self._tmop_prm(h, gamma, dlim), _ptr(x), _ptr(u),
+                                                  _ptr(y), _stream()))
+
+    def tmop_hessian_diag(self, x, diag, h, gamma=0.0, dlim=1.0):
+        self._check(self.lib.lh_tmop_hessian_diag(self.h, self._tmop_prm(h, gamma, dlim), _ptr(x), _ptr(diag),
+                                                  _stream()))
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))

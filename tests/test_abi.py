@@ -28,6 +28,7 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(lh.LhCgInfo) == 32
     assert ctypes.sizeof(lh.LhParams) == 64
     assert ctypes.sizeof(lh.LhRemapInfo) == 32
+    assert ctypes.sizeof(lh.LhTmopParams) == 24
 
 
 def test_setup_rejects_bad_arguments_without_a_gpu():
