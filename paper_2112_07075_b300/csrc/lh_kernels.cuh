@@ -1537,9 +1537,9 @@ struct Family {
       k.cCC = n2 * it * it * it;
       k.cdC = -0.5 * n2 * it * it;
     } else {
-      const double c13 = cbrt(tau);
-      const double r = 1.0 / (c13 * c13);   // tau^(-2/3)
-      const double it = 1.0 / tau;
+      const double rc = rcbrt(tau);          // tau^(-1/3)
+      const double r = rc * rc;              // tau^(-2/3)
+      const double it = r * rc;              // 1/tau
       k.mu = n2 * r * (1.0 / 3.0) - 1.0;
       k.cT = (2.0 / 3.0) * r;
       k.cC = -(2.0 / 9.0) * n2 * r * it;
