@@ -24,6 +24,16 @@ Energy source (2D Taylor-Green only): b_j = sum_q omega rho0 detJ0 Q(x_q) phi_j
 with Q = (3 pi / 8)(cos 3pi x cos pi y - cos pi x cos 3pi y) at the current
 quadrature-point positions.
 
+Shock workload (reading of the Sedov blast, used to exercise the viscosity's
+linear term and the step control): rho0 = 1, v0 = 0, internal energy E0 = 0.25
+deposited uniformly in the element at the origin corner (e = E0 / its mass, 0
+elsewhere); the box faces are the symmetry planes (v.n = 0).
+Step control with rejection (controlled_step): the attempt uses
+dt = min(c, dt_est(S_n), t_end - t) (c <= 0: no cap); if the CFL estimate at the
+half-step state S_h is smaller than dt, the attempt is rejected (state
+unchanged) and c = 0.85 dt_est(S_h) (0.5 dt if S_h has an inverted element);
+otherwise it is accepted and a finite c grows by 2 %.
+
 Pins (tests/test_oracle_hydro.py): total energy KE + IE - sum dt 1^T b is
 conserved to round-off with direct solves; total mass 1^T M 1 is constant;
 a uniform state at rest stays exactly at rest; 2D Taylor-Green with source and
@@ -105,7 +115,9 @@ def tg2d_source(X):
 PROBLEMS = {
     "taylor_green": (tg_velocity, tg_pressure),
     "gresho": (gresho_velocity, lambda X: gresho_pressure(X)),
+    "sedov": (lambda X: np.zeros_like(X), None),   # energy set element-wise below
 }
+SEDOV_E0 = 0.25
 
 
 @dataclass
@@ -156,6 +168,10 @@ class Hydro:
         x = m.x0.copy()
         v = vel(x)
         v = np.where(m.free, v, 0.0)               # exact BC on constrained DOFs
+        if problem == "sedov":                     # E0 in the corner element at the origin
+            e = np.zeros((m.NE, m.NL1))
+            e[0, :] = SEDOV_E0 / float(np.sum(self.rho0detJ0[0] * T.w))
+            return x, v, e
         Xq = h1_values(T, m.gather(x))             # [NE, Q, d]
         Xq_t = np.transpose(Xq, (2, 0, 1))
         rho0 = self.rho0detJ0 / self.detJ0
@@ -250,6 +266,36 @@ class Hydro:
         a, vb, de, b, _ = self._stage(xh, vh, eh, v, dt)
         info = StepInfo(dt=dt, dt_est=dt_est, energy_source=dt * float(np.sum(b)))
         return x + dt * vb, v + dt * a, e + dt * de, info
+
+
+def controlled_step(hy, x, v, e, t, t_end, c):
+    """One attempt of a CFL step with rejection (see the module docstring).
+
+    Returns (x, v, e, StepInfo) with extra = {rejected, dt_est_half, c}; a
+    rejected attempt returns the input state unchanged.
+    """
+    e = e.reshape(hy.mesh.NE, hy.mesh.NL1)
+    D, dt_est, _ = hy.qdata(x, v, e)
+    dt = min(dt_est, t_end - t)
+    if c > 0.0:
+        dt = min(dt, c)
+    if not dt > 0.0:
+        raise RuntimeError("non-positive time step (inverted element?)")
+    F = hy.force_matrix(D)
+    a0 = hy.mass_solve(-(F @ np.ones(hy.mesh.NL2)).reshape(v.shape))
+    vb0 = v + 0.5 * dt * a0
+    b0 = hy.energy_source(x)
+    de0 = hy.energy_solve((F.T @ vb0.ravel()).reshape(b0.shape) + b0)
+    xh, vh, eh = x + 0.5 * dt * vb0, vb0, e + 0.5 * dt * de0
+    a, vb, de, b, dt_half = hy._stage(xh, vh, eh, v, dt)
+    if dt_half < dt:
+        c_new = 0.85 * dt_half if dt_half > 0.0 else 0.5 * dt
+        return x, v, e, StepInfo(dt=dt, dt_est=dt_est,
+                                 extra={"rejected": True, "dt_est_half": dt_half, "c": c_new})
+    c_new = 1.02 * c if c > 0.0 else c
+    info = StepInfo(dt=dt, dt_est=dt_est, energy_source=dt * float(np.sum(b)),
+                    extra={"rejected": False, "dt_est_half": dt_half, "c": c_new})
+    return x + dt * vb, v + dt * a, e + dt * de, info
 
 
 def _cg(A, b, tol):
