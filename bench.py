@@ -354,8 +354,10 @@ def run_ours(args):
     remap = None
     stiffness = None
     tmop = None
+    shock = None
     if not args.no_forms and world == 1:
-        which = ("precision", "batching", "learned", "remap", "stiffness", "tmop") if args.forms == "all" \
+        which = ("precision", "batching", "learned", "remap", "stiffness", "tmop", "shock") \
+            if args.forms == "all" \
             else (args.forms,)
         forms = forms_report(flush) if "precision" in which else None
         batching = batching_report(flush) if "batching" in which else None
@@ -363,6 +365,7 @@ def run_ours(args):
         remap = remap_report(flush) if "remap" in which else None
         stiffness = stiffness_report(flush) if "stiffness" in which else None
         tmop = tmop_report(flush) if "tmop" in which else None
+        shock = shock_report(flush) if "shock" in which else None
     clk.__exit__()
     clocks = clk.summary()
     clocks["window"] = "sampled every 200 ms from warm-up to the end of the GPU measurements"
@@ -388,6 +391,7 @@ def run_ours(args):
             "remap": remap,
             "stiffness": stiffness,
             "tmop": tmop,
+            "shock": shock,
             "cg_iters_last_step": list(si.cg_iters), "sim_time": si.t, "dt_last": si.dt,
             "device_status": status, "wall_s_timed": wall,
         }
@@ -868,6 +872,59 @@ def tmop_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
     return out
 
 
+def shock_report(flush, n=24, p=2, q1=4, t_end=0.05, max_attempts=2000):
+    """Shock workload: 3D Sedov blast (E0 = 0.25 in the corner element, gamma = 1.4) on
+    n^3 Q2 hexes, CFL 0.5 steps with the step control and rejection, from t = 0 to
+    t_end. Every attempt (accepted or rejected) is timed with events (L2 flushed before
+    it); value = vector DOFs x accepted steps / total time of all attempts."""
+    import torch
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context
+    dim = 3
+    V = inputs.box_vertices(dim, n)
+    ctx = Context(dim, n, V, p, q1, gamma=1.4, cfl=0.5)
+    ctx.set_dt_control(True)
+    x, v, e = ctx.init_state("sedov")
+    info = ctx.new_step_info(0.0, t_end)
+    stream = torch.cuda.current_stream()
+    ev = []
+    attempts, chunk = 0, 16
+    while attempts < max_attempts:
+        # chunks of 16 attempts; step by step near t_end so that no attempt runs past it
+        for _ in range(chunk):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(10.0)
+            a.record(stream)
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+            b.record(stream)
+            ev.append((a, b))
+            attempts += 1
+        si = ctx.read_step_info(info)
+        left = t_end - si.t
+        if left <= 1e-12 * t_end or si.status != 0:
+            break
+        chunk = 16 if left > 40.0 * si.dt else 1
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    si = ctx.read_step_info(info)
+    st = ctx.sync_status()
+    sz = ctx.sizes
+    real = si.steps + si.rejections
+    total = sum(ms)
+    vm = v.norm(dim=0)
+    gmax = int(torch.argmax(vm).item())
+    r_peak = float(x[:, gmax].norm().item())
+    out = {"workload": f"3D Sedov blast, {n}^3 hexes, Q{p}/Q{p - 1}, {q1}^3 Gauss points, gamma 1.4, CFL 0.5, "
+                       f"step control with rejection, t = 0 -> {t_end}",
+           "accepted_steps": si.steps, "rejected_attempts": si.rejections, "t_final": si.t, "status": st,
+           "total_ms": total, "ms_per_attempt": total / max(1, real),
+           "mdofs": sz.nv * si.steps / (total * 1e-3) / 1e6,
+           "cg_iters_per_solve": si.cg_iters_total / max(1, 2 * real),
+           "radius_of_max_speed": r_peak, "max_speed": float(vm.max().item())}
+    ctx.close()
+    return out
+
+
 def remap_cpu_baseline(n=12):
     """The oracle's remap (global assembly, direct solves) on one pseudo-time step of
     an n^3 Q2 mesh with a smooth displacement (a bounded sample: LU of the 3D mass
@@ -960,7 +1017,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--forms", default="all",
-                    choices=["all", "precision", "batching", "learned", "remap", "stiffness", "tmop"],
+                    choices=["all", "precision", "batching", "learned", "remap", "stiffness", "tmop", "shock"],
                     help="which form reports to add (default all; --no-forms for none)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir", "bf16tc_ir"],
                     help="mass-solve precision of the main arm (the headline workload is FP64)")

@@ -65,7 +65,14 @@ typedef enum {
   LH_ERR_UNSUPPORTED = 7    /* (dim, order, q1) combination not compiled */
 } lh_status;
 
-typedef enum { LH_PROBLEM_TAYLOR_GREEN = 0, LH_PROBLEM_GRESHO = 1 } lh_problem;
+typedef enum {
+  LH_PROBLEM_TAYLOR_GREEN = 0,
+  LH_PROBLEM_GRESHO = 1,    /* 2D only */
+  LH_PROBLEM_SEDOV = 2      /* blast: rho0 = 1, v0 = 0, internal energy 0.25 deposited uniformly in
+                               element 0 (the corner at the origin), e = 0 elsewhere; the box
+                               faces are symmetry planes. Exercises the viscosity's linear term
+                               and the step control (lh_set_dt_control). */
+} lh_problem;
 typedef enum { LH_SOURCE_NONE = 0, LH_SOURCE_TAYLOR_GREEN_2D = 1 } lh_source;
 typedef enum { LH_PRECISION_FP64 = 0, LH_PRECISION_FP32_IR = 1, LH_PRECISION_BF16TC_IR = 2 } lh_precision;
 
@@ -125,6 +132,11 @@ typedef struct {
   int steps;          /* steps taken with this record */
   long long cg_iters_total; /* sum of cg_iters over all steps taken with this record
                                (lh_rk2avg_step only; the batch step leaves it alone) */
+  /* step control with rejection (lh_set_dt_control); untouched otherwise */
+  double dt_ctl;      /* controller cap c on dt (<= 0: none); the caller may start it at 0 */
+  double dt_est_half; /* CFL estimate at the half-step state of the last attempt */
+  int rejected;       /* 1 if the last attempt was rejected (state left unchanged) */
+  int rejections;     /* rejected attempts with this record */
 } lh_step_info;
 
 typedef struct lh_ctx lh_ctx;
@@ -224,6 +236,18 @@ lh_status lh_energy_solve(lh_ctx *ctx, const double *rhs, double *out, lh_stream
  * warm-started from the previous solve's acceleration. */
 lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt,
                          double rel_tol, int max_it, lh_step_info *info, lh_stream_t stream);
+
+/* Step control with rejection for the CFL-controlled steps (dt <= 0) of
+ * lh_rk2avg_step (no counterpart in the paper, which names no integrator; used by
+ * shock workloads). With it enabled, an attempt takes dt = min(info->dt_ctl (if > 0),
+ * dt_est(S_n), t_end - t); the stage-2 quadrature update also estimates the CFL step
+ * at the half-step state S_h. If dt_est(S_h) < dt the attempt is rejected on the
+ * device: x, v, e stay unchanged, t does not advance, info->rejected = 1,
+ * info->rejections += 1 and dt_ctl = 0.85 dt_est(S_h) (0.5 dt if S_h is inverted);
+ * otherwise the step is taken as usual and a positive dt_ctl grows by 2 %. The
+ * caller repeats calls until info->t reaches t_end. enable = 0 restores plain CFL
+ * steps. Returns LH_ERR_ARG for a NULL context. */
+lh_status lh_set_dt_control(lh_ctx *ctx, int enable);
 
 /* Solver timing probe (measurement support; no counterpart in the paper).
  * lh_timing_enable(ctx, 1) makes every later mass solve of this context

@@ -16,6 +16,9 @@ using namespace lh;
 namespace {
 
 constexpr int kNodeThreads = 256;
+static_assert(sizeof(lh_step_info) == 104, "lh_step_info layout is part of the ABI");
+static_assert(sizeof(lh_cg_info) == 32 && sizeof(lh_remap_info) == 32 && sizeof(lh_tmop_params) == 24,
+              "info/parameter layouts are part of the ABI");
 
 struct Zs { double z[5]; };
 
@@ -89,7 +92,7 @@ __global__ void k_init_v(MeshDesc m, int dim, int problem, const double *__restr
         vv[1] = -cos(pi * X) * sin(pi * Y) * cos(pi * Z);
         vv[2] = 0.0;
       }
-    } else {
+    } else if (problem == LH_PROBLEM_GRESHO) {
       const double r = sqrt(X * X + Y * Y);
       const double vt = r < 0.2 ? 5.0 * r : (r < 0.4 ? 2.0 - 5.0 * r : 0.0);
       const double rs = r > 0.0 ? r : 1.0;
@@ -101,6 +104,22 @@ __global__ void k_init_v(MeshDesc m, int dim, int problem, const double *__restr
       x[k] = x0[k];
       v[k] = constrained(m, dim, g, c) ? 0.0 : vv[c];
     }
+  }
+}
+
+// Sedov blast energy: e = E0 / (mass of element 0) on element 0, 0 elsewhere
+// (every thread of element 0 sums its mass data in the same order).
+constexpr double kSedovE0 = 0.25;
+__global__ void k_init_sedov_e(int ne, int nl, int nq, const double *__restrict__ mq, double *__restrict__ e) {
+  const size_t n = (size_t)ne * nl;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    double val = 0.0;
+    if (k < (size_t)nl) {
+      double mass = 0.0;
+      for (int q = 0; q < nq; ++q) mass += mq[q];
+      val = kSedovE0 / mass;
+    }
+    e[k] = val;
   }
 }
 
@@ -131,8 +150,10 @@ __global__ void k_rk_mid(size_t nv, const double *__restrict__ x, const double *
 }
 
 // Final update: vb = v + dt/2 a, x += dt vb, v += dt a.
+// With step control, `rejected` set leaves the state alone.
 __global__ void k_rk_final(size_t nv, double *__restrict__ x, double *__restrict__ v, const double *__restrict__ a,
-                           const double *__restrict__ dtp, double *__restrict__ vbo) {
+                           const double *__restrict__ dtp, double *__restrict__ vbo, const int *rejected) {
+  if (rejected && *rejected) return;
   const double dt = *dtp, hdt = 0.5 * dt;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (size_t)gridDim.x * blockDim.x) {
     const double ak = a[k], vk = v[k];
@@ -148,7 +169,13 @@ __global__ void k_to_float(size_t n, const double *__restrict__ a, float *__rest
     b[k] = (float)a[k];
 }
 
-__global__ void k_step_finish(lh_step_info *info, const int *status, int has_source) {
+__global__ void k_step_finish(lh_step_info *info, const int *status, int has_source, int controlled) {
+  if (controlled && info->rejected) {   // nothing advances; the solver work is counted
+    info->rejections += 1;
+    info->cg_iters_total += (long long)info->cg_iters[0] + info->cg_iters[1];
+    info->status = *status;
+    return;
+  }
   info->t += info->dt;
   info->steps += 1;
   info->cg_iters_total += (long long)info->cg_iters[0] + info->cg_iters[1];
@@ -428,13 +455,19 @@ lh_status lh_sync_status(lh_ctx *ctx) {
 
 lh_status lh_init_state(lh_ctx *ctx, int problem, double *x, double *v, double *e, lh_stream_t stream) {
   if (!ctx || !x || !v || !e) return ctx ? fail(ctx, LH_ERR_ARG, "null state pointer") : LH_ERR_ARG;
-  if (problem != LH_PROBLEM_TAYLOR_GREEN && problem != LH_PROBLEM_GRESHO)
+  if (problem != LH_PROBLEM_TAYLOR_GREEN && problem != LH_PROBLEM_GRESHO && problem != LH_PROBLEM_SEDOV)
     return fail(ctx, LH_ERR_ARG, "unknown problem");
   if (problem == LH_PROBLEM_GRESHO && ctx->dim != 2) return fail(ctx, LH_ERR_ARG, "Gresho is 2D only");
   cudaStream_t s = (cudaStream_t)stream;
   k_init_v<<<grid_for(ctx->mesh.nh1, kNodeThreads, 65535), kNodeThreads, 0, s>>>(ctx->mesh, ctx->dim, problem,
                                                                                   ctx->x0, x, v);
   if (lh_status st = check_launch(ctx, "init v")) return st;
+  if (problem == LH_PROBLEM_SEDOV) {
+    const size_t n = (size_t)ctx->mesh.ne * ctx->nl;
+    k_init_sedov_e<<<grid_for(n, kNodeThreads, 65535), kNodeThreads, 0, s>>>(ctx->mesh.ne, ctx->nl, ctx->nq,
+                                                                               ctx->mq, e);
+    return check_launch(ctx, "init e");
+  }
   InitEArgs ia{ctx->mesh, ctx->tab, ctx->x0, ctx->mq, ctx->rho0, ctx->me_inv, e, ctx->prm.gamma, problem};
   ctx->ops->init_e(ia, ctx->grid_elem, s);
   return check_launch(ctx, "init e");
@@ -460,6 +493,7 @@ static void fill_qdata(lh_ctx *c, QdataArgs &a, const double *x, const double *v
   a.counter = c->counter;
   a.dt_est_out = nullptr;
   a.step = nullptr;
+  a.ctl = 0;
   a.status = c->dstatus;
 }
 
@@ -605,6 +639,12 @@ static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int 
   return LH_OK;
 }
 
+lh_status lh_set_dt_control(lh_ctx *ctx, int enable) {
+  if (!ctx) return LH_ERR_ARG;
+  ctx->dt_control = enable != 0;
+  return LH_OK;
+}
+
 lh_status lh_timing_enable(lh_ctx *ctx, int enable) {
   if (!ctx) return LH_ERR_ARG;
   if (enable && !ctx->tev[0]) {
@@ -679,12 +719,14 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
   const Ops &o = *c->ops;
   const double *dtp = &info->dt;
   const bool src = c->prm.source == LH_SOURCE_TAYLOR_GREEN_2D;
+  const bool ctl = c->dt_control && !(dt > 0.0);   // step control with rejection
   // ---- stage 1 at S_n
   QdataArgs qa;
   fill_qdata(c, qa, x, v, e);
   qa.want_dt = 1;
   qa.fixed_dt = dt;
   qa.step = info;
+  qa.ctl = ctl ? 1 : 0;
   o.qdata(qa, c->grid_elem, s);
   if (lh_status st = check_launch(c, "qdata 1")) return st;
   if (lh_status st = force_impl(c, nullptr, c->rhs, -1.0, c->invdiag, s)) return st;
@@ -709,8 +751,13 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
   fa.out = c->eh;
   o.force_t(fa, c->grid_elem, s);
   if (lh_status st = check_launch(c, "force_t 1")) return st;
-  // ---- stage 2 at S_half
+  // ---- stage 2 at S_half (with step control: CFL estimate there, accept or reject)
   fill_qdata(c, qa, c->xh, c->vh, c->eh);
+  if (ctl) {
+    qa.want_dt = 1;
+    qa.step = info;
+    qa.ctl = 2;
+  }
   o.qdata(qa, c->grid_elem, s);
   if (lh_status st = check_launch(c, "qdata 2")) return st;
   if (lh_status st = force_impl(c, nullptr, c->rhs, -1.0, c->invdiag, s)) return st;
@@ -719,7 +766,8 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
                              &info->cg_rel_res[1], s))
     return st;
   if (lh_status st = lh::learn_after_solve(c, s)) return st;
-  k_rk_final<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x, v, c->a_prev, dtp, c->vb);
+  k_rk_final<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, x, v, c->a_prev, dtp, c->vb,
+                                                    ctl ? &info->rejected : nullptr);
   if (lh_status st = check_launch(c, "rk final")) return st;
   fa.v = c->vb;
   fa.src_x = src ? c->xh : nullptr;
@@ -728,9 +776,10 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
   fa.partials = c->partials;
   fa.counter = c->counter;
   fa.src_sum = src ? &info->energy_src : nullptr;
+  fa.skip = ctl ? &info->rejected : nullptr;
   o.force_t(fa, c->grid_elem, s);
   if (lh_status st = check_launch(c, "force_t 2")) return st;
-  k_step_finish<<<1, 1, 0, s>>>(info, c->dstatus, src ? 1 : 0);
+  k_step_finish<<<1, 1, 0, s>>>(info, c->dstatus, src ? 1 : 0, ctl ? 1 : 0);
   return check_launch(c, "step finish");
 }
 

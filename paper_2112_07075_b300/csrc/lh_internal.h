@@ -36,6 +36,7 @@ struct QdataArgs {
   unsigned int *counter;     // last-block ticket (reset by the last block)
   double *dt_est_out;        // optional
   lh_step_info *step;        // optional: dt control of lh_rk2avg_step
+  int ctl;                   // step control with rejection: 0 off, 1 stage 1 (choose dt), 2 stage 2 (decide)
   int *status;
 };
 
@@ -56,6 +57,7 @@ struct ForceTArgs {
   double *partials;          // for the source sum
   unsigned int *counter;
   double *src_sum;           // optional: dt * sum_j b_j
+  const int *skip;           // optional: nonzero -> the launch does nothing (rejected step)
 };
 
 struct MassArgs {
@@ -259,6 +261,7 @@ struct lh_ctx {
   void *bar = nullptr;   // lh::GridBarrier
   int *dstatus = nullptr;
   lh_cg_info *remap_ci = nullptr;   // result of the remap's latest mass solve
+  bool dt_control = false;          // lh_set_dt_control
   lh_learn *learn = nullptr;   // learned-form state (lh_learn_attach), or NULL
   // solver timing probe (lh_timing_enable): event pairs around solver launches
   static constexpr int kTimingPairs = 64;

@@ -499,11 +499,25 @@ struct Family {
       const double dt_est = mx > 0.0 ? a.cfl / mx : (mx == 0.0 ? INFINITY : 0.0);
       if (a.dt_est_out) *a.dt_est_out = dt_est;
       if (a.step) {
-        a.step->dt_est = dt_est;
-        double dt = a.fixed_dt;
-        if (!(dt > 0.0)) dt = fmin(dt_est, a.step->t_end - a.step->t);
-        if (!(dt > 0.0)) dt = 0.0;
-        a.step->dt = dt;
+        lh_step_info *s = a.step;
+        if (a.ctl == 2) {   // half-step state: accept or reject the attempt
+          const double dt = s->dt;
+          s->dt_est_half = dt_est;
+          const int rej = dt_est < dt;
+          s->rejected = rej;
+          if (rej) s->dt_ctl = dt_est > 0.0 ? 0.85 * dt_est : 0.5 * dt;
+          else if (s->dt_ctl > 0.0) s->dt_ctl *= 1.02;
+        } else {
+          s->dt_est = dt_est;
+          double dt = a.fixed_dt;
+          if (!(dt > 0.0)) {
+            dt = fmin(dt_est, s->t_end - s->t);
+            if (a.ctl == 1 && s->dt_ctl > 0.0) dt = fmin(dt, s->dt_ctl);
+          }
+          if (!(dt > 0.0)) dt = 0.0;
+          s->dt = dt;
+          if (a.ctl == 1) s->rejected = 0;
+        }
       }
     }
   }
@@ -550,6 +564,7 @@ struct Family {
     return sizeof(double) * (TAB + 2 * CX * ND + FT_S + DIM * CX * NQ + CX * NQ + NB * NQ + NB * NL + RED);
   }
   static __device__ __forceinline__ void body_force_t(const ForceTArgs &a, int e0) {
+    if (a.skip && *a.skip) return;   // uniform over the grid: the step was rejected
     extern __shared__ double sm[];
     double *st = sm, *u = st + TAB, *xu = u + CX * ND, *S = xu + CX * ND, *g = S + FT_S;
     double *xq = g + DIM * CX * NQ, *sq = xq + CX * NQ, *out = sq + NB * NQ, *red = out + NB * NL;

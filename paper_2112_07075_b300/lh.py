@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "liblh.so")
 LH_OK, LH_ERR_ARG, LH_ERR_CUDA, LH_ERR_OOM, LH_ERR_INVERTED, LH_ERR_NOT_CONVERGED, LH_ERR_TIMEOUT, \
     LH_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["ok", "argument", "cuda", "out of memory", "inverted", "not converged", "timeout", "unsupported"]
-PROBLEMS = {"taylor_green": 0, "gresho": 1}
+PROBLEMS = {"taylor_green": 0, "gresho": 1, "sedov": 2}
 SOURCES = {"none": 0, "tg2d": 1}
 PRECISIONS = {"fp64": 0, "fp32_ir": 1, "bf16tc_ir": 2}
 
@@ -32,7 +32,8 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_learn_attach",
             "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc",
             "lh_remap_velocity", "lh_remap_apply", "lh_stiffness_setup", "lh_stiffness_mult", "lh_laplacian",
-            "lh_tmop_objective", "lh_tmop_gradient", "lh_tmop_hessian_mult", "lh_tmop_hessian_diag"]
+            "lh_tmop_objective", "lh_tmop_gradient", "lh_tmop_hessian_mult", "lh_tmop_hessian_diag",
+            "lh_set_dt_control"]
 
 
 class LhParams(ctypes.Structure):
@@ -56,7 +57,9 @@ class LhStepInfo(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("t_end", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dt_est", ctypes.c_double), ("energy_src", ctypes.c_double),
                 ("cg_rel_res", ctypes.c_double * 2), ("cg_iters", ctypes.c_int * 2),
-                ("status", ctypes.c_int), ("steps", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong)]
+                ("status", ctypes.c_int), ("steps", ctypes.c_int), ("cg_iters_total", ctypes.c_longlong),
+                ("dt_ctl", ctypes.c_double), ("dt_est_half", ctypes.c_double), ("rejected", ctypes.c_int),
+                ("rejections", ctypes.c_int)]
 
 
 class LhTmopParams(ctypes.Structure):
@@ -116,6 +119,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
         "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
         "lh_timing_enable": (I, [P, I]),
+        "lh_set_dt_control": (I, [P, I]),
         "lh_mass_mult_tc": (I, [P, VP, VP, VP]),
         "lh_remap_velocity": (I, [P, VP, VP, VP, I, I, D, I, VP, VP]),
         "lh_remap_apply": (I, [P, VP, VP, D, VP, VP, VP, VP]),
@@ -336,6 +340,10 @@ class Context:
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))
+
+    def set_dt_control(self, enable: bool = True) -> None:
+        """Step control with rejection for CFL steps (lh_set_dt_control)."""
+        self._check(self.lib.lh_set_dt_control(self.h, 1 if enable else 0))
 
     def timing_enable(self, enable: bool = True) -> None:
         """Record CUDA events around every later mass-solver launch (lh_timing_enable)."""

@@ -24,7 +24,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_sizes_match_the_header():
-    assert ctypes.sizeof(lh.LhStepInfo) == 80
+    assert ctypes.sizeof(lh.LhStepInfo) == 104
     assert ctypes.sizeof(lh.LhCgInfo) == 32
     assert ctypes.sizeof(lh.LhParams) == 64
     assert ctypes.sizeof(lh.LhRemapInfo) == 32
