@@ -399,6 +399,12 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline(wl, V)
             if remap is not None:
                 remap["cpu_baseline"] = remap_cpu_baseline()
+            if stiffness is not None:
+                stiffness["cpu_baseline"] = stiffness_cpu_baseline()
+            if tmop is not None:
+                tmop["cpu_baseline"] = tmop_cpu_baseline()
+            if shock is not None:
+                shock["cpu_baseline"] = shock_cpu_baseline()
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -923,6 +929,74 @@ def shock_report(flush, n=24, p=2, q1=4, t_end=0.05, max_attempts=2000):
            "radius_of_max_speed": r_peak, "max_speed": float(vm.max().item())}
     ctx.close()
     return out
+
+
+def stiffness_cpu_baseline(n=12):
+    """The oracle's stiffness action (element matrices + global assembly + product) and
+    Laplacian (LU of M_x) of a velocity-like field on an n^3 Q2 mesh with a smooth
+    displacement: one of each, timed together."""
+    from oracle.fem import Tables
+    from oracle.mesh import Mesh
+    from oracle.stiffness import Stiffness
+    from paper_2112_07075_b300 import inputs
+    m = Mesh(inputs.box_vertices(3, n), 3, n, 2)
+    x = m.x0 + 0.01 * np.sin(3.0 * m.x0[::-1])
+    v = inputs.uniform(8, (3, m.NH1), -1.0, 1.0)
+    t0 = time.perf_counter()
+    st = Stiffness(m, Tables(3, 2, 4), x)
+    st.mult(v)
+    t1 = time.perf_counter()
+    st.laplacian(v)
+    t2 = time.perf_counter()
+    return {"value": 3 * m.NH1 / (t1 - t0) / 1e6, "unit": "MDOF/s (setup + action)", "cores": _cores(),
+            "kind": "oracle", "laplacian_s": t2 - t1,
+            "sample": f"{n}^3 Q2: assembly + one action {t1 - t0:.1f} s, Laplacian (LU) {t2 - t1:.1f} s"}
+
+
+def tmop_cpu_baseline(n=24):
+    """The oracle's TMOP objective and gradient (explicit sums) on the benchmark's
+    24^3 Q2 mesh (jittered stand-in for the Lagrangian mesh) and its assembled Hessian
+    action on an 8^3 sample (the dense element Hessians grow as NE x (3 x 27)^2)."""
+    from oracle.fem import Tables
+    from oracle.mesh import Mesh
+    from oracle.tmop import Tmop
+    from paper_2112_07075_b300 import inputs
+    out = {}
+    for nn, what in ((n, "grad"), (8, "hess")):
+        m = Mesh(inputs.box_vertices(3, nn, jitter=0.1, seed=3), 3, nn, 2)
+        x0 = Mesh(inputs.box_vertices(3, nn), 3, nn, 2).x0
+        tm = Tmop(m, Tables(3, 2, 4), np.eye(3) / nn, x0, gamma=0.1, dlim=0.5 / nn)
+        t0 = time.perf_counter()
+        if what == "grad":
+            tm.objective(m.x0)
+            tm.gradient(m.x0)
+        else:
+            tm.hessian_mult(m.x0, m.x0)
+        out[what] = (time.perf_counter() - t0, 3 * m.NH1)
+    tg, ng = out["grad"]
+    th, nh = out["hess"]
+    return {"value": ng / tg / 1e6, "unit": "MDOF/s (objective + gradient)", "cores": _cores(), "kind": "oracle",
+            "hessian_mult_mdofs_8cubed": nh / th / 1e6,
+            "sample": f"objective + gradient at {n}^3 Q2 {tg:.1f} s; Hessian assembly + action at 8^3 {th:.1f} s"}
+
+
+def shock_cpu_baseline(n=8, attempts=6):
+    """The oracle's controlled steps of the 3D Sedov blast on an n^3 Q2 mesh."""
+    from oracle.hydro import Hydro, Params, controlled_step
+    from paper_2112_07075_b300 import inputs
+    hy = Hydro(Params(dim=3, n=n, order=2, q1=4, vertices=inputs.box_vertices(3, n), gamma=1.4, cfl=0.5))
+    x, v, e = hy.initial_state("sedov")
+    t, c, acc = 0.0, 0.0, 0
+    t0 = time.perf_counter()
+    for _ in range(attempts):
+        x, v, e, info = controlled_step(hy, x, v, e, t, 1.0, c)
+        c = info.extra["c"]
+        if not info.extra["rejected"]:
+            t += info.dt
+            acc += 1
+    dt = time.perf_counter() - t0
+    return {"value": 3 * hy.mesh.NH1 * acc / dt / 1e6, "unit": "MDOF/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{attempts} controlled attempts ({acc} accepted) of 3D Sedov at {n}^3 Q2, {dt:.1f} s"}
 
 
 def remap_cpu_baseline(n=12):
