@@ -273,7 +273,8 @@ lh_status lh_timing_read(lh_ctx *ctx, double *solver_ms, int *solves);
  * partially assembled: per stage one element pass computes omega detJ(tau) and
  * omega adj(J(tau)) u at the quadrature points and applies K element by element
  * with sum factorization; M(tau) is inverted by the Lagrange phase's persistent
- * Jacobi-PCG (FP64 whatever the context's precision).
+ * solver in the context's precision (FP64 Jacobi-PCG, or the FP32 / tensor-core
+ * inner solver under FP64 refinement), always to the FP64 residual criterion.
  * ------------------------------------------------------------------------- */
 
 /* Result of one lh_remap_velocity call; lives in DEVICE memory, reset by the call. */
@@ -294,9 +295,9 @@ typedef struct {
  *     k1 = M(tau)^-1 K(tau) v,   k2 = M(tau + h/2)^-1 K(tau + h/2) (v + h/2 k1),
  *     v <- v + h k2.
  * constrained != 0: the Lagrange phase's v.n = 0 DOFs keep their value (the solves
- * act on the free DOFs); 0: every DOF is remapped. Mass solves: FP64 Jacobi-PCG to
- * rel_tol (<= 0: 1e-12) and max_it (<= 0: 1000), warm-started from the previous
- * stage's rate. info: DEVICE lh_remap_info or NULL.
+ * act on the free DOFs); 0: every DOF is remapped. Mass solves: the context's
+ * solver (see lh_mass_cg) to rel_tol (<= 0: 1e-12) and max_it (<= 0: 1000),
+ * warm-started from the previous stage's rate. info: DEVICE lh_remap_info or NULL.
  * Works in the context's solver and stage scratch and in its force quadrature data
  * buffer: call lh_update_qdata again before a later lh_force_mult/lh_force_mult_t.
  * v must not alias x0 or x1 (LH_ERR_ARG). */
@@ -336,8 +337,9 @@ lh_status lh_stiffness_setup(lh_ctx *ctx, const double *x, lh_stream_t stream);
 lh_status lh_stiffness_mult(lh_ctx *ctx, const double *u, double *y, lh_stream_t stream);
 
 /* Discrete Laplacian of an H1 field (natural boundary conditions): lap solves
- * M_x lap = -S_x v per component with the FP64 Jacobi-PCG on every DOF, stopping at
- * ||b - M x||_2 <= rel_tol ||b||_2 (rel_tol <= 0: 1e-12; max_it <= 0: 1000).
+ * M_x lap = -S_x v per component on every DOF with the context's solver (see
+ * lh_mass_cg), stopping at ||b - M x||_2 <= rel_tol ||b||_2 (rel_tol <= 0: 1e-12;
+ * max_it <= 0: 1000).
  * v, lap: DEVICE [dim][N_H1], must not alias; lap in = initial guess.
  * info: DEVICE lh_cg_info or NULL. LH_ERR_ARG before the first lh_stiffness_setup. */
 lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol, int max_it,

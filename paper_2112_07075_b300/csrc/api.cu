@@ -328,6 +328,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {&c->xh, NV},                    {&c->vh, NV},                {&c->vb, NV},
       {&c->eh, NE * c->nl},            {&c->partials, npart},         {&c->zv, NV},
       {&c->stiff_G, NE * (dim * (dim + 1) / 2) * NQ}, {&c->stiff_mq, NE * NQ}, {&c->stiff_inv, NV},
+      {(double **)&c->stiff_mq32, nf * (NE * NQ + 1) / 2}, {(double **)&c->stiff_inv32, nf * (NV + 1) / 2},
       {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
       {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
       {(double **)&c->ap32, nf * (NV + 1) / 2},       {(double **)&c->d32, nf * (NV + 1) / 2},
@@ -559,20 +560,23 @@ constexpr int kMaxOuter = 40;
 constexpr int kMaxInner = 200;
 
 // mq_r, inv_r: mass data and Jacobi inverse of another mass matrix on the same mesh
-// topology (the remap's M(tau)); the solve then runs the FP64 solver with them.
+// topology (the remap's M(tau), the Laplacian's M_x); with their FP32 copies
+// mq32_r, inv32_r the context's precision form solves with them, without them the
+// FP64 solver does.
 static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
                            int *iters_out, double *relres_out, cudaStream_t s, const double *mq_r,
-                           const double *inv_r) {
-  if (!mq_r && (c->prm.precision == LH_PRECISION_FP32_IR || c->prm.precision == LH_PRECISION_BF16TC_IR)) {
+                           const double *inv_r, const float *mq32_r, const float *inv32_r) {
+  if ((!mq_r || mq32_r) &&
+      (c->prm.precision == LH_PRECISION_FP32_IR || c->prm.precision == LH_PRECISION_BF16TC_IR)) {
     const bool tcf = c->prm.precision == LH_PRECISION_BF16TC_IR;
     CgIrArgs a{};
     a.mesh = c->mesh;
     a.tab = c->tab;
-    a.mq = c->mq;
-    a.invdiag = c->invdiag;
+    a.mq = mq_r ? mq_r : c->mq;
+    a.invdiag = mq_r ? inv_r : c->invdiag;
     a.b = b;
-    a.mq32 = c->mq32;
-    a.invdiag32 = c->invdiag32;
+    a.mq32 = mq_r ? mq32_r : c->mq32;
+    a.invdiag32 = mq_r ? inv32_r : c->invdiag32;
     a.x = x;
     a.evec = c->evec;
     a.partials = c->partials;
@@ -625,11 +629,12 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
 // brackets the solver launch on its stream.
 static lh_status cg_impl(lh_ctx *c, const double *b, double *x, double tol, int max_it, lh_cg_info *info,
                          int *iters_out, double *relres_out, cudaStream_t s, const double *mq_r = nullptr,
-                         const double *inv_r = nullptr) {
+                         const double *inv_r = nullptr, const float *mq32_r = nullptr,
+                         const float *inv32_r = nullptr) {
   const bool rec = c->timing && c->timing_n < lh_ctx::kTimingPairs;
   if (rec && cudaEventRecord(c->tev[2 * c->timing_n], s) != cudaSuccess)
     return fail(c, LH_ERR_CUDA, "timing event record");
-  const lh_status st = cg_launch(c, b, x, tol, max_it, info, iters_out, relres_out, s, mq_r, inv_r);
+  const lh_status st = cg_launch(c, b, x, tol, max_it, info, iters_out, relres_out, s, mq_r, inv_r, mq32_r, inv32_r);
   if (st != LH_OK) return st;
   if (rec) {
     if (cudaEventRecord(c->tev[2 * c->timing_n + 1], s) != cudaSuccess)
@@ -789,15 +794,28 @@ lh_status lh_rk2avg_step(lh_ctx *ctx, double *x, double *v, double *e, double dt
 // Scratch of a remap call (all of it free between Lagrange steps): the stage rate k
 // and the displacement in the RK2 stage vectors, M(tau)'s Jacobi inverse in vb, its
 // mass data and element diagonal in the force quadrature data buffer.
+// With a precision form, FP32 copies of M(tau)'s data and Jacobi inverse follow
+// (64-byte aligned: the tensor-core solver bulk-copies the mass data, which needs 16).
 struct RemapScratch {
   double *u, *k, *inv, *mq, *dvec;
+  float *mq32, *inv32;
 };
+static size_t align_doubles(size_t n) { return (n + 7) / 8 * 8; }
 static RemapScratch remap_scratch(lh_ctx *c) {
-  return {c->xh, c->vh, c->vb, c->D, c->D + (size_t)c->mesh.ne * c->nq};
+  const size_t nq = (size_t)c->mesh.ne * c->nq, nd = (size_t)c->mesh.ne * c->nd;
+  double *dv = c->D + align_doubles(nq);
+  float *m32 = (float *)(dv + align_doubles(nd));
+  float *i32 = m32 + align_doubles(nq) * 2;
+  return {c->xh, c->vh, c->vb, c->D, dv, m32, i32};
 }
-// mq [NE][NQ] and the element diagonal [NE][ND] must fit in the quadrature data
-// buffer [NE][dim*dim][NQ]: (dim^2 - 1) q1^dim >= (p+1)^dim, true for q1 >= p+1
-static bool remap_fits(const lh_ctx *c) { return (size_t)(c->dim * c->dim - 1) * c->nq >= (size_t)c->nd; }
+// all of it must fit in the quadrature data buffer [NE][dim*dim][NQ] (true for q1 >= p+1)
+static bool remap_fits(const lh_ctx *c) {
+  const size_t nq = (size_t)c->mesh.ne * c->nq, nd = (size_t)c->mesh.ne * c->nd;
+  size_t need = align_doubles(nq) + align_doubles(nd);
+  if (c->prm.precision != LH_PRECISION_FP64) need += align_doubles(nq) + align_doubles(c->nv / 2 + 1);
+  return need <= (size_t)c->mesh.ne * c->dim * c->dim * c->nq;
+}
+static bool precision_form(const lh_ctx *c) { return c->prm.precision != LH_PRECISION_FP64; }
 
 }  // extern "C"
 namespace {
@@ -853,7 +871,16 @@ static lh_status remap_stage(lh_ctx *c, const RemapScratch &r, const double *x0,
   if (lh_status st = check_launch(c, "remap element pass")) return st;
   c->ops->remap_nodes(c->mesh, c->evec, r.dvec, constrained, c->rhs, r.inv, c->grid_node, kNodeThreads, s);
   if (lh_status st = check_launch(c, "remap node pass")) return st;
-  if (lh_status st = cg_impl(c, c->rhs, r.k, tol, max_it, ci, nullptr, nullptr, s, r.mq, r.inv)) return st;
+  const bool pf = precision_form(c);
+  if (pf) {   // FP32 copies for the inner solver of the precision form
+    const size_t nq = (size_t)c->mesh.ne * c->nq;
+    k_to_float<<<grid_for(nq, kNodeThreads, 65535), kNodeThreads, 0, s>>>(nq, r.mq, r.mq32);
+    k_to_float<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, r.inv, r.inv32);
+    if (lh_status st = check_launch(c, "remap fp32 copies")) return st;
+  }
+  if (lh_status st = cg_impl(c, c->rhs, r.k, tol, max_it, ci, nullptr, nullptr, s, r.mq, r.inv,
+                             pf ? r.mq32 : nullptr, pf ? r.inv32 : nullptr))
+    return st;
   if (!info) return LH_OK;
   k_remap_solved<<<1, 1, 0, s>>>(info, ci, c->dstatus);
   return check_launch(c, "remap info");
@@ -947,6 +974,12 @@ lh_status lh_stiffness_setup(lh_ctx *ctx, const double *x, lh_stream_t stream) {
   if (lh_status st = check_launch(c, "stiffness setup")) return st;
   c->ops->remap_nodes(c->mesh, nullptr, c->evec, 0, nullptr, c->stiff_inv, c->grid_node, kNodeThreads, s);
   if (lh_status st = check_launch(c, "stiffness diagonal")) return st;
+  if (precision_form(c)) {   // FP32 copies for the inner solver of the precision form
+    const size_t nq = (size_t)c->mesh.ne * c->nq;
+    k_to_float<<<grid_for(nq, kNodeThreads, 65535), kNodeThreads, 0, s>>>(nq, c->stiff_mq, c->stiff_mq32);
+    k_to_float<<<c->grid_node, kNodeThreads, 0, s>>>(c->nv, c->stiff_inv, c->stiff_inv32);
+    if (lh_status st = check_launch(c, "stiffness fp32 copies")) return st;
+  }
   c->stiff_ready = true;
   return LH_OK;
 }
@@ -982,7 +1015,8 @@ lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol
   lh_ctx *c = ctx;
   cudaStream_t s = (cudaStream_t)stream;
   if (lh_status st = stiff_apply(c, v, c->rhs, -1.0, s)) return st;   // rhs = -S v
-  return cg_impl(c, c->rhs, lap, rel_tol, max_it, info, nullptr, nullptr, s, c->stiff_mq, c->stiff_inv);
+  return cg_impl(c, c->rhs, lap, rel_tol, max_it, info, nullptr, nullptr, s, c->stiff_mq, c->stiff_inv,
+                 c->stiff_mq32, c->stiff_inv32);
 }
 
 // ---------------------------------------------------------------------------

@@ -252,6 +252,7 @@ struct lh_ctx {
   // stiffness operator on a mesh set by lh_stiffness_setup: PA data, unit-density mass
   // data and its Jacobi inverse (every DOF)
   double *stiff_G = nullptr, *stiff_mq = nullptr, *stiff_inv = nullptr;
+  float *stiff_mq32 = nullptr, *stiff_inv32 = nullptr;   // precision form only
   bool stiff_ready = false;
   float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
         *evec32 = nullptr;

@@ -185,3 +185,27 @@ def test_remap_after_lagrange_steps_full_size():
         ref = ref + h * k2
     assert np.max(np.abs(out - ref)) <= REMAP_TOL * np.max(np.abs(ref))
     assert np.max(np.abs(ref - v_lag)) > 1e-6 * np.max(np.abs(v_lag))   # the remap did something
+
+
+@pytest.mark.parametrize("precision,dim,p,q1,n,steps,constrained",
+                         [("fp32_ir", 2, 2, 4, 6, 2, True), ("fp32_ir", 3, 2, 4, 3, 1, False),
+                          ("bf16tc_ir", 3, 4, 6, 3, 1, True), ("bf16tc_ir", 3, 3, 6, 4, 2, False)])
+def test_remap_in_precision_forms_matches_oracle(precision, dim, p, q1, n, steps, constrained):
+    """The remap's mass solves in the context's precision form reach the FP64 residual
+    criterion, so the result is held to the precision forms' field bar (1e-10)."""
+    from paper_2112_07075_b300.lh import Context
+    V0 = inputs.box_vertices(dim, n, jitter=0.12, seed=1)
+    m0 = Mesh(V0, dim, n, p)
+    m1 = Mesh(inputs.box_vertices(dim, n, jitter=0.12, seed=2), dim, n, p)
+    ctx = Context(dim, n, V0, p, q1, precision=precision)
+    v0 = inputs.uniform(33, (dim, m0.NH1), -1.0, 1.0)
+    if constrained:
+        v0 = np.where(m0.free, v0, 0.0)
+    ref = Remap(m0, Tables(dim, p, q1), m0.x0, m1.x0, constrained=constrained).remap(v0, steps)
+    vd = _dev(v0)
+    info = ctx.new_remap_info()
+    ctx.remap_velocity(_dev(m0.x0), _dev(m1.x0), vd, steps, constrained, rel_tol=1e-13, info=info)
+    ri = ctx.read_remap_info(info)
+    assert ri.status == 0 and ri.solves == 2 * steps and ri.cg_rel_res_max <= 1e-13
+    assert np.max(np.abs(_np(vd) - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert ctx.sync_status() == 0

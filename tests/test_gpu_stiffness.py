@@ -139,3 +139,22 @@ def test_full_size_lagrangian_mesh():
         sol, flag = spla.cg(st.M, -ref[c], rtol=1e-14, maxiter=2000, M=Minv)
         assert flag == 0
         assert np.max(np.abs(laps[c] - sol)) <= 1e-11 * np.max(np.abs(sol))
+
+
+@pytest.mark.parametrize("precision,dim,p,q1,n", [("fp32_ir", 2, 2, 4, 6), ("fp32_ir", 3, 2, 4, 3),
+                                                  ("bf16tc_ir", 3, 4, 6, 3), ("bf16tc_ir", 3, 3, 6, 4)])
+def test_laplacian_in_precision_forms_matches_oracle(precision, dim, p, q1, n):
+    from paper_2112_07075_b300.lh import Context
+    V = inputs.box_vertices(dim, n, jitter=0.12, seed=5)
+    m = Mesh(V, dim, n, p)
+    x = m.x0 + 0.02 / n * np.sin(2.0 * np.pi * m.x0[::-1])
+    ctx = Context(dim, n, V, p, q1, precision=precision)
+    v = inputs.uniform(43, (dim, m.NH1), -1.0, 1.0)
+    ref = Stiffness(m, Tables(dim, p, q1), x).laplacian(v)
+    ctx.stiffness_setup(_dev(x))
+    lap = ctx.h1_vector()
+    info = ctx.new_cg_info()
+    ctx.laplacian(_dev(v), lap, rel_tol=1e-13, max_it=5000, info=info)
+    ci = ctx.read_cg_info(info)
+    assert ci.status == 0 and ci.rel_res <= 1e-13 and ci.refinements >= 1
+    assert np.max(np.abs(_np(lap) - ref)) <= 1e-10 * np.max(np.abs(ref))
