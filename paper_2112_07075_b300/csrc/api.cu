@@ -328,6 +328,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {&c->xh, NV},                    {&c->vh, NV},                {&c->vb, NV},
       {&c->eh, NE * c->nl},            {&c->partials, npart},         {&c->zv, NV},
       {&c->stiff_G, NE * (dim * (dim + 1) / 2) * NQ}, {&c->stiff_mq, NE * NQ}, {&c->stiff_inv, NV},
+      {(double **)&c->ncopy, (NH1 * (1u << dim) * sizeof(int) + 7) / 8},
       {(double **)&c->stiff_mq32, nf * (NE * NQ + 1) / 2}, {(double **)&c->stiff_inv32, nf * (NV + 1) / 2},
       {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
       {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
@@ -374,6 +375,8 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   gll_nodes(p, z.z);
   k_nodes_x0<<<grid_for(NH1, kNodeThreads, 65535), kNodeThreads>>>(m, dim, p, z, c->verts, c->x0);
   if (lh_status s = check_launch(c, "nodes")) return s;
+  o.node_table(m, c->ncopy, grid_for(NH1, kNodeThreads, 65535), kNodeThreads, 0);
+  if (lh_status s = check_launch(c, "node table")) return s;
 
   // ---- geometry at qpoints
   GeomArgs ga{m, c->tab, c->x0, rho0_q, c->rho0, c->mq, c->jinv0, c->partials, c->dstatus};
@@ -596,6 +599,7 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
     a.max_outer = kMaxOuter;
     a.max_inner = kMaxInner;
     a.kimg = c->kimg;
+    a.ncopy = c->ncopy;
     const cudaError_t e = tcf ? c->ops->cg_tc(a, c->grid_cg_tc, s) : c->ops->cg_ir(a, c->grid_cg_ir, s);
     if (e != cudaSuccess) return fail(c, LH_ERR_CUDA, std::string("cg_ir launch: ") + cudaGetErrorString(e));
     return check_launch(c, "cg_ir");
@@ -611,6 +615,7 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
   a.p = c->pv;
   a.ap = c->ap;
   a.z = c->zv;
+  a.ncopy = c->ncopy;
   a.evec = c->evec;
   a.partials = c->partials;
   a.bar = c->bar;

@@ -71,6 +71,7 @@ struct CgArgs {
   const double *tab, *mq, *invdiag, *b;
   double *x, *r, *p, *ap, *evec, *partials;
   double *z;                 // invdiag * r, kept with r
+  const int *ncopy;          // [N_H1][2^DIM] E-vector offsets e*DIM*ND + i of each node's copies, -1 padded
   void *bar;                 // GridBarrier
   int *status;
   lh_cg_info *info;
@@ -94,6 +95,7 @@ struct CgIrArgs {
   double tol, inner_tol;
   int max_it, max_outer, max_inner;
   const void *kimg;   // tensor-core form: shared-memory image of the BF16 interpolation matrix
+  const int *ncopy;   // as in CgArgs
 };
 
 struct GeomArgs {
@@ -208,6 +210,8 @@ struct Ops {
   size_t smem_tmop[4];
   void *k_tmop[4];
   void (*tmop)(int mode, const TmopArgs &, int grid, cudaStream_t);
+  // setup: the node-copy table of the solvers' node sweeps
+  void (*node_table)(const MeshDesc &, int *ncopy, int grid, int threads, cudaStream_t);
 };
 
 const Ops *find_ops_2d(int p, int q1);
@@ -261,6 +265,7 @@ struct lh_ctx {
   unsigned int *counter = nullptr;
   void *bar = nullptr;   // lh::GridBarrier
   int *dstatus = nullptr;
+  int *ncopy = nullptr;   // [N_H1][2^dim] E-vector offsets of each node's copies (CgArgs::ncopy)
   lh_cg_info *remap_ci = nullptr;   // result of the remap's latest mass solve
   bool dt_control = false;          // lh_set_dt_control
   lh_learn *learn = nullptr;   // learned-form state (lh_learn_attach), or NULL

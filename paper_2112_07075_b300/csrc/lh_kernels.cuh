@@ -89,6 +89,17 @@ __device__ __forceinline__ int node_copies(const MeshDesc &m, int g, int C, int 
   return n;
 }
 
+// Row g of the node-copy table (offsets e*DIM*ND + i of node g's copies, -1 padded).
+template <int DIM>
+__device__ __forceinline__ void node_table_row(const int *__restrict__ tab, int g, int (&off)[1 << DIM]) {
+  const int4 a = __ldg(reinterpret_cast<const int4 *>(tab + (size_t)g * (1 << DIM)));
+  off[0] = a.x; off[1] = a.y; off[2] = a.z; off[3] = a.w;
+  if constexpr (DIM == 3) {
+    const int4 b = __ldg(reinterpret_cast<const int4 *>(tab + (size_t)g * 8 + 4));
+    off[4] = b.x; off[5] = b.y; off[6] = b.z; off[7] = b.w;
+  }
+}
+
 // Is H1 node g constrained for velocity component c (v.n = 0 on the box faces)?
 template <int DIM>
 __device__ __forceinline__ bool h1_constrained(const MeshDesc &m, int g, int c) {
@@ -917,41 +928,33 @@ struct Family {
       __syncthreads();
       const double alpha = s_sc[4];
       {  // one node sweep: q = M p_new gathered, p = p_new, x += alpha p, r -= alpha q,
-         // z = invdiag r, r.r and r.z (all loads of a component before any use)
+         // z = invdiag r, r.r and r.z; one (node, component) per work item, its
+         // copies located through the node-copy table, every load issued first
         double acc[2] = {0.0, 0.0};
-        for (int g = gtid; g < nh1; g += gstride) {
-          int off[1 << DIM] = {};
-          const int n = node_copies<DIM, D>(m, g, DIM, off);
-          double idg[DIM], pv[DIM], zv[DIM];
+        for (int k = gtid; k < DIM * nh1; k += gstride) {
+          const int c = DIM == 2 ? (k >= nh1 ? 1 : 0) : (k >= 2 * nh1 ? 2 : (k >= nh1 ? 1 : 0));
+          const int g = k - c * nh1;
+          int off[1 << DIM];
+          node_table_row<DIM>(a.ncopy, g, off);
+          const double idg = __ldg(a.invdiag + k);
+          const double pv = a.p[k], zv = a.z[k], xv = a.x[k], rv = a.r[k];
+          double ev[1 << DIM];
 #pragma unroll
-          for (int c = 0; c < DIM; ++c) {
-            const int k = c * nh1 + g;
-            idg[c] = __ldg(a.invdiag + k);
-            pv[c] = a.p[k];
-            zv[c] = a.z[k];
-          }
+          for (int j = 0; j < (1 << DIM); ++j) ev[j] = off[j] >= 0 ? a.evec[off[j] + c * ND] : 0.0;
+          double qv = ev[0];
 #pragma unroll
-          for (int c = 0; c < DIM; ++c) {   // one component's copies at a time (register budget)
-            const int k = c * nh1 + g;
-            const double xv = a.x[k], rv = a.r[k];
-            double ev[1 << DIM];
-#pragma unroll
-            for (int j = 0; j < (1 << DIM); ++j) ev[j] = j < n ? a.evec[off[j] + c * ND] : 0.0;
-            double qv = ev[0];
-#pragma unroll
-            for (int j = 1; j < (1 << DIM); ++j)
-              if (j < n) qv += ev[j];
-            if (idg[c] != 0.0) {   // constrained DOFs keep p = r = z = 0
-              const double pn = fma(beta, pv[c], zv[c]);
-              const double r2 = fma(-alpha, qv, rv);
-              const double z2 = r2 * idg[c];
-              a.p[k] = pn;
-              a.x[k] = fma(alpha, pn, xv);
-              a.r[k] = r2;
-              a.z[k] = z2;
-              acc[0] = fma(r2, r2, acc[0]);
-              acc[1] = fma(z2, r2, acc[1]);
-            }
+          for (int j = 1; j < (1 << DIM); ++j)
+            if (off[j] >= 0) qv += ev[j];
+          if (idg != 0.0) {   // constrained DOFs keep p = r = z = 0
+            const double pn = fma(beta, pv, zv);
+            const double r2 = fma(-alpha, qv, rv);
+            const double z2 = r2 * idg;
+            a.p[k] = pn;
+            a.x[k] = fma(alpha, pn, xv);
+            a.r[k] = r2;
+            a.z[k] = z2;
+            acc[0] = fma(r2, r2, acc[0]);
+            acc[1] = fma(z2, r2, acc[1]);
           }
         }
         bsum<2>(acc, red);
@@ -1170,37 +1173,54 @@ struct Family {
         __syncthreads();
         const float alpha = s_f[2];
         {  // one node sweep: q = M p_new gathered, p = p_new, d += alpha p, r -= alpha q,
-           // r.r and r.z (all loads of a node issued before any use)
+           // r.r and r.z; one (node, component) per work item, copies through the
+           // node-copy table, every load issued first
           float acc[5] = {0, 0, 0, 0, 0};
-          for (int g = gtid; g < nh1; g += gstride) {
-            int off[1 << DIM] = {};
-            const int n = node_copies<DIM, D>(m, g, DIM, off);
-            float idg[DIM], pv[DIM], rv[DIM], dv[DIM], ev[DIM][1 << DIM];
+          // U work items per pass, all of their loads in flight together. High orders
+          // (p >= 3) run one large CTA per SM and many items per thread: overlap 4;
+          // low orders keep the register count that allows two CTAs per SM.
+          constexpr int U = P >= 3 ? 4 : 1;
+          const int nvk = DIM * nh1;
+          for (int k0 = gtid; k0 < nvk; k0 += U * gstride) {
+            int kk[U], cc[U], off[U][1 << DIM];
+            float idg[U], pv[U], rv[U], dv[U], ev[U][1 << DIM];
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) {
-              const int k = c * nh1 + g;
-              idg[c] = __ldg(a.invdiag32 + k);
-              pv[c] = a.p32[k];
-              rv[c] = a.r32[k];
-              dv[c] = a.d32[k];
+            for (int u = 0; u < U; ++u) {
+              const int k = k0 + u * gstride;
+              kk[u] = k;
+              const bool ok = k < nvk;
+              const int kc = ok ? k : 0;
+              cc[u] = DIM == 2 ? (kc >= nh1 ? 1 : 0) : (kc >= 2 * nh1 ? 2 : (kc >= nh1 ? 1 : 0));
+              node_table_row<DIM>(a.ncopy, kc - cc[u] * nh1, off[u]);
+              if (!ok) {
 #pragma unroll
-              for (int j = 0; j < (1 << DIM); ++j) ev[c][j] = j < n ? a.evec32[off[j] + c * ND] : 0.0f;
+                for (int j = 0; j < (1 << DIM); ++j) off[u][j] = -1;
+              }
+              idg[u] = ok ? __ldg(a.invdiag32 + kc) : 0.0f;
+              pv[u] = a.p32[kc];
+              rv[u] = a.r32[kc];
+              dv[u] = a.d32[kc];
             }
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) {
-              const int k = c * nh1 + g;
-              float qv = ev[c][0];
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+              for (int j = 0; j < (1 << DIM); ++j)
+                ev[u][j] = off[u][j] >= 0 ? a.evec32[off[u][j] + cc[u] * ND] : 0.0f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              float qv = ev[u][0];
 #pragma unroll
               for (int j = 1; j < (1 << DIM); ++j)
-                if (j < n) qv += ev[c][j];
-              if (idg[c] != 0.0f) {   // constrained DOFs keep p = r = d = 0
-                const float pn = fmaf(beta, pv[c], idg[c] * rv[c]);
-                const float r2 = fmaf(-alpha, qv, rv[c]);
+                if (off[u][j] >= 0) qv += ev[u][j];
+              if (idg[u] != 0.0f) {   // constrained DOFs (and items past the end) keep p = r = d
+                const int k = kk[u];
+                const float pn = fmaf(beta, pv[u], idg[u] * rv[u]);
+                const float r2 = fmaf(-alpha, qv, rv[u]);
                 a.p32[k] = pn;
-                a.d32[k] = fmaf(alpha, pn, dv[c]);
+                a.d32[k] = fmaf(alpha, pn, dv[u]);
                 a.r32[k] = r2;
                 acc[0] = fmaf(r2, r2, acc[0]);
-                acc[1] = fmaf(r2 * idg[c], r2, acc[1]);
+                acc[1] = fmaf(r2 * idg[u], r2, acc[1]);
               }
             }
           }

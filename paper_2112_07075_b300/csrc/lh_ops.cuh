@@ -34,6 +34,17 @@ __global__ void k_remap_nodes(MeshDesc m, const double *__restrict__ evec, const
   }
 }
 
+// Node-copy table: for node g, the offsets e*DIM*ND + i of its element-local
+// copies in a DIM-component E-vector, in node_copies order, padded with -1.
+template <int DIM, int D>
+__global__ void k_node_table(MeshDesc m, int *__restrict__ tab) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < m.nh1; g += gridDim.x * blockDim.x) {
+    int off[1 << DIM];
+    const int n = node_copies<DIM, D>(m, g, DIM, off);
+    for (int j = 0; j < (1 << DIM); ++j) tab[(size_t)g * (1 << DIM) + j] = j < n ? off[j] : -1;
+  }
+}
+
 template <int DIM, int P, int Q>
 struct OpsBuilder {
   using F = Family<DIM, P, Q>;
@@ -139,6 +150,9 @@ struct OpsBuilder {
       default: k_tmop<DIM, P, Q, 3><<<grid, F::THREADS, F::tmop_smem(3), s>>>(a); break;
     }
   }
+  static void node_table(const MeshDesc &m, int *tab, int grid, int threads, cudaStream_t s) {
+    k_node_table<DIM, P + 1><<<grid, threads, 0, s>>>(m, tab);
+  }
   static const Ops *get() {
     static const Ops ops = {DIM, P, Q, F::NB, F::THREADS, F::NBC, F::TC,
                             F::qdata_smem(), F::force_smem(), F::force_t_smem(), F::mass_smem(), F::cg_smem(),
@@ -157,7 +171,7 @@ struct OpsBuilder {
                             {F::tmop_smem(0), F::tmop_smem(1), F::tmop_smem(2), F::tmop_smem(3)},
                             {(void *)k_tmop<DIM, P, Q, 0>, (void *)k_tmop<DIM, P, Q, 1>, (void *)k_tmop<DIM, P, Q, 2>,
                              (void *)k_tmop<DIM, P, Q, 3>},
-                            &tmop};
+                            &tmop, &node_table};
     return &ops;
   }
 };
