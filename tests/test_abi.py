@@ -45,3 +45,21 @@ def test_setup_rejects_bad_arguments_without_a_gpu():
     prm.order, prm.source = 2, 1
     prm.dim = 3
     assert lib.lh_setup(ctypes.byref(prm), None, ctypes.byref(h)) == lh.LH_ERR_ARG
+
+
+def test_widened_entry_points_reject_null_arguments_without_a_gpu():
+    """The remap, stiffness, TMOP and step-control calls check their arguments on the
+    host before anything is enqueued (no device is touched)."""
+    lib = lh.load_library()
+    E = lh.LH_ERR_ARG
+    prm = lh.LhTmopParams(0.25, 0.0, 1.0)
+    assert lib.lh_remap_velocity(None, None, None, None, 1, 1, 0.0, 0, None, None) == E
+    assert lib.lh_remap_apply(None, None, None, 0.5, None, None, None, None) == E
+    assert lib.lh_stiffness_setup(None, None, None) == E
+    assert lib.lh_stiffness_mult(None, None, None, None) == E
+    assert lib.lh_laplacian(None, None, None, 0.0, 0, None, None) == E
+    assert lib.lh_tmop_objective(None, ctypes.byref(prm), None, None, None, None) == E
+    assert lib.lh_tmop_gradient(None, ctypes.byref(prm), None, None, None, None) == E
+    assert lib.lh_tmop_hessian_mult(None, ctypes.byref(prm), None, None, None, None) == E
+    assert lib.lh_tmop_hessian_diag(None, ctypes.byref(prm), None, None, None) == E
+    assert lib.lh_set_dt_control(None, 1) == E
