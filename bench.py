@@ -284,12 +284,16 @@ def run_ours(args):
     cgi = ctx.read_cg_info(cginfo)
     t_ft = timed(lambda: ctx.force_mult_t(v, out))
     cg_flops = cgi.iters * W["cg_iter_flops"] + W["mass_flops"]
+    # rates in the mini-app's convention (H1 vector DOFs or qpoints per second, 1e6/s):
+    # force = NV per (F.1, F^T v) pair, mass = NV x CG iterations, qdata = NQ per update
     kernels = {
         "mass_cg": {"ms": t_cg, "iters": cgi.iters, "gflop": cg_flops / 1e9,
-                    "tflops": cg_flops / (t_cg * 1e-3) / 1e12},
-        "qdata": {"ms": t_q},
+                    "tflops": cg_flops / (t_cg * 1e-3) / 1e12,
+                    "mass_rate_mdofs": sz.nv * cgi.iters / (t_cg * 1e-3) / 1e6},
+        "qdata": {"ms": t_q, "rate_mqs": sz.nq / (t_q * 1e-3) / 1e6},
         "force_mult": {"ms": t_f, "tflops": W["force_flops"] / (t_f * 1e-3) / 1e12},
         "force_mult_t": {"ms": t_ft, "tflops": W["force_t_flops"] / (t_ft * 1e-3) / 1e12},
+        "force_pair": {"rate_mdofs": sz.nv / ((t_f + t_ft) * 1e-3) / 1e6},
     }
     # Roofline of the dominant kernel, measured live over the timed steps: the
     # library's event pairs around each solver launch (same stream) give its
