@@ -878,10 +878,17 @@ def tmop_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
             ts.append(a.elapsed_time(b))
         return statistics.median(ts[1:])
 
+    work = ctx.tmop_workspace()
+    ypa = ctx.h1_vector()
     t = {"objective": timed(lambda: ctx.tmop_objective(x, x_init, F, **kw)),
          "gradient": timed(lambda: ctx.tmop_gradient(x, x_init, g, **kw)),
          "hessian_mult": timed(lambda: ctx.tmop_hessian_mult(x, u, y, **kw)),
-         "hessian_diag": timed(lambda: ctx.tmop_hessian_diag(x, dg, **kw))}
+         "hessian_diag": timed(lambda: ctx.tmop_hessian_diag(x, dg, **kw)),
+         "hessian_setup_pa": timed(lambda: ctx.tmop_hessian_setup(x, work, **kw)),
+         "hessian_mult_pa": timed(lambda: ctx.tmop_hessian_mult_pa(work, u, ypa, **kw))}
+    pa_diff = float((ypa - y).norm() / y.norm())
+    pa_mb = work.numel() * 8 / 1e6
+    del work
     st = ctx.sync_status()
     sz = ctx.sizes
     D, Q = p + 1, q1
@@ -889,10 +896,15 @@ def tmop_report(flush, lagrange_steps=50, reps=5, wl_name="tg3d_24_q2"):
     interp = Q * D ** 3 + Q * Q * D * D + Q ** 3 * D if dim == 3 else Q * D * D + Q * Q * D
     npair = dim * (dim + 1) // 2
     # contraction FMAs per element (the pointwise metric work comes on top)
+    nq_ = Q ** dim
     fma = {"objective": dim * (grad + interp), "gradient": dim * (2 * grad + 2 * interp),
-           "hessian_mult": dim * (3 * grad + 2 * interp), "hessian_diag": dim * grad + (npair * dim + 1) * interp}
+           "hessian_mult": dim * (3 * grad + 2 * interp), "hessian_diag": dim * grad + (npair * dim + 1) * interp,
+           "hessian_setup_pa": dim * grad,
+           "hessian_mult_pa": dim * (2 * grad + 2 * interp) + nq_ * (dim * dim) ** 2}
     out = {"workload": f"{wl['desc']}; Lagrangian mesh after {lagrange_steps} CFL steps, x0 = the initial mesh",
-           "params": kw, "objective_value": float(F.item()), "status": st}
+           "params": kw, "objective_value": float(F.item()), "status": st,
+           "pa_workspace_mb": pa_mb, "pa_vs_matrix_free_rel_diff": pa_diff,
+           "pa_speedup_per_product": t["hessian_mult"] / t["hessian_mult_pa"]}
     for k, ms in t.items():
         out[k] = {"ms": ms, "contraction_gflop": 2 * sz.ne * fma[k] / 1e9,
                   "contraction_tflops": 2 * sz.ne * fma[k] / (ms * 1e-3) / 1e12}

@@ -383,6 +383,21 @@ lh_status lh_tmop_hessian_mult(lh_ctx *ctx, const lh_tmop_params *prm, const dou
 lh_status lh_tmop_hessian_diag(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, double *diag,
                                lh_stream_t stream);
 
+/* Partially assembled Hessian, for the repeated Hessian products of a Newton-Krylov
+ * solve at fixed x (a departure from Section 3.4's fully matrix-free choice: on this
+ * GPU the FP64 rate, not memory, bounds the recomputation of the metric).
+ * lh_tmop_workspace_size: the workspace length in doubles, NE * n(n+1)/2 * q1^dim
+ * with n = dim^2 (the symmetric second-derivative tensor of mu per quadrature point,
+ * scaled by w_q det W / h^2). lh_tmop_hessian_setup fills the caller's DEVICE
+ * workspace at x (LH_ERR_INVERTED latched for det T <= 0); lh_tmop_hessian_mult_pa
+ * then gives y = (d^2F/dx^2) u from it (limiting term included, same prm), equal to
+ * lh_tmop_hessian_mult at that x up to rounding. work must not alias x, u or y. */
+lh_status lh_tmop_workspace_size(const lh_ctx *ctx, int64_t *doubles);
+lh_status lh_tmop_hessian_setup(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, double *work,
+                                lh_stream_t stream);
+lh_status lh_tmop_hessian_mult_pa(lh_ctx *ctx, const lh_tmop_params *prm, const double *work,
+                                  const double *u, double *y, lh_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Batching form: many independent problems advanced together.
  *

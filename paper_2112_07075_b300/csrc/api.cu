@@ -282,7 +282,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
   LH_CUDA(c, cudaFuncSetAttribute(o.k_stiff_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)o.smem_stiff_setup));
   LH_CUDA(c, cudaFuncSetAttribute(o.k_stiff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_stiff));
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 6; ++k)
     LH_CUDA(c, cudaFuncSetAttribute(o.k_tmop[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)o.smem_tmop[k]));
   c->grid_elem = (m.ne + o.nb - 1) / o.nb;
   int occ = 0;
@@ -1093,6 +1093,37 @@ lh_status lh_tmop_hessian_diag(lh_ctx *ctx, const lh_tmop_params *prm, const dou
   if (lh_status st = tmop_args(ctx, prm, x, a)) return st;
   if (diag == x) return fail(ctx, LH_ERR_ARG, "diag must not alias x");
   return tmop_vector(ctx, 3, a, diag, (cudaStream_t)stream);
+}
+
+lh_status lh_tmop_workspace_size(const lh_ctx *ctx, int64_t *doubles) {
+  if (!ctx || !doubles) return LH_ERR_ARG;
+  const int64_t nr = (int64_t)ctx->dim * ctx->dim;
+  *doubles = (int64_t)ctx->mesh.ne * (nr * (nr + 1) / 2) * ctx->nq;
+  return LH_OK;
+}
+
+lh_status lh_tmop_hessian_setup(lh_ctx *ctx, const lh_tmop_params *prm, const double *x, double *work,
+                                lh_stream_t stream) {
+  if (!ctx || !work) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  TmopArgs a;
+  if (lh_status st = tmop_args(ctx, prm, x, a)) return st;
+  if (work == x) return fail(ctx, LH_ERR_ARG, "work must not alias x");
+  a.pa = work;
+  ctx->ops->tmop(4, a, ctx->grid_elem, (cudaStream_t)stream);
+  return check_launch(ctx, "tmop Hessian setup");
+}
+
+lh_status lh_tmop_hessian_mult_pa(lh_ctx *ctx, const lh_tmop_params *prm, const double *work, const double *u,
+                                  double *y, lh_stream_t stream) {
+  if (!ctx || !work || !u || !y) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
+  if (!prm) return fail(ctx, LH_ERR_ARG, "null pointer");
+  if (y == u || y == work) return fail(ctx, LH_ERR_ARG, "y must not alias u or the workspace");
+  TmopArgs a;
+  if (lh_status st = tmop_args(ctx, prm, u, a)) return st;   // x is not read by the action
+  a.x = nullptr;
+  a.u = u;
+  a.pa = const_cast<double *>(work);
+  return tmop_vector(ctx, 5, a, y, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -151,6 +151,7 @@ struct TmopArgs {
   double h_inv, detW;  // target W = h I: 1/h, h^DIM
   double lim;          // gamma / d^2 (0: no limiting term)
   double *evec;        // gradient / Hessian action / diagonal: [NE][DIM][ND]
+  double *pa;          // partially assembled Hessian data [NE][NH2][NQ] (setup writes, apply reads)
   double *partials;    // objective: block sums, last-block total into *out
   unsigned int *counter;
   double *out;
@@ -206,9 +207,10 @@ struct Ops {
   void *k_stiff_setup, *k_stiff;
   void (*stiff_setup)(const StiffArgs &, int grid, cudaStream_t);
   void (*stiff)(const StiffArgs &, int grid, cudaStream_t);
-  // TMOP element passes, mode 0 objective, 1 gradient, 2 Hessian action, 3 diagonal
-  size_t smem_tmop[4];
-  void *k_tmop[4];
+  // TMOP element passes, mode 0 objective, 1 gradient, 2 Hessian action, 3 diagonal,
+  // 4 partially assembled Hessian setup, 5 its action
+  size_t smem_tmop[6];
+  void *k_tmop[6];
   void (*tmop)(int mode, const TmopArgs &, int grid, cudaStream_t);
   // setup: the node-copy table of the solvers' node sweeps
   void (*node_table)(const MeshDesc &, int *ncopy, int grid, int threads, cudaStream_t);

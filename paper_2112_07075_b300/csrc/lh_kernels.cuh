@@ -1815,6 +1815,111 @@ struct Family {
     for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) a.evec[(size_t)e0 * DIM * ND + k] = xu[k];
   }
 
+  // ----- partially assembled Hessian (a B300 variant of Eq. 7 for repeated products) -----
+  // setup: per qpoint the symmetric 2nd-derivative tensor of mu, scaled by w det W / h^2,
+  // as the upper triangle of the (a n) x (b p) matrix: [NE][NH2][NQ];
+  // apply: y_e = sum_q ghat^T (H : ghat u) + the limiting term, from that data.
+  static constexpr int NR = DIM * DIM;
+  static constexpr int NH2 = NR * (NR + 1) / 2;
+  static __device__ __forceinline__ int hidx(int r, int s) { return r * NR - r * (r - 1) / 2 + (s - r); }
+  // d C_an / d T_bp (the cofactor's derivative; C_an does not depend on row a of T)
+  static __device__ __forceinline__ double dcof(const double *T, int a, int n, int b, int p) {
+    if constexpr (DIM == 2) {
+      return (b == 1 - a && p == 1 - n) ? (a == n ? 1.0 : -1.0) : 0.0;
+    } else {
+      if (a == b || n == p) return 0.0;
+      const int c = 3 - a - b, q = 3 - n - p;
+      const double s1 = (b - a + 3) % 3 == 1 ? 1.0 : -1.0, s2 = (p - n + 3) % 3 == 1 ? 1.0 : -1.0;
+      return s1 * s2 * T[c * 3 + q];
+    }
+  }
+  static __device__ __forceinline__ void body_tmop_pa_setup(const TmopArgs &a, int e0) {
+    extern __shared__ double sm[];
+    double *st = sm, *xu = st + TAB, *S = xu + 2 * CX * ND, *g = S + TM_S;
+    const MeshDesc &m = a.mesh;
+    const int nb = min(NB, m.ne - e0);
+    load_tab(st, a.tab);
+    gather_elem(xu, a.x, DIM, m, e0, nb);
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(xu, g, S, st + oB, st + oG);
+    const double hi = a.h_inv;
+    for (int k = threadIdx.x; k < nb * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      double Tm[NR], C[NR];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) Tm[c * DIM + l] = hi * g[(l * CX + b * DIM + c) * NQ + q];
+      const double tau = cofactor(Tm, C);
+      if (!(tau > 0.0)) latch_status(a.status, 4);
+      double n2 = 0.0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) n2 = fma(Tm[r], Tm[r], n2);
+      const MetricCoef mc = metric(n2, tau);
+      double w, iw;
+      qweight(st, q, w, iw);
+      const double f = w * a.detW * hi * hi;
+      double *He = a.pa + (size_t)(e0 + b) * NH2 * NQ + q;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int s = r; s < NR; ++s) {
+          const int ai = r / DIM, ni = r % DIM, bi = s / DIM, pi = s % DIM;
+          double h = mc.cTC * fma(Tm[r], C[s], Tm[s] * C[r]) + mc.cCC * C[r] * C[s] + mc.cdC * dcof(Tm, ai, ni, bi, pi);
+          if (r == s) h += mc.cZ;
+          He[(size_t)hidx(r, s) * NQ] = f * h;
+        }
+    }
+  }
+  static __device__ __forceinline__ void body_tmop_pa_apply(const TmopArgs &a, int e0) {
+    extern __shared__ double sm[];
+    double *st = sm, *uu = st + TAB, *yv = uu + CX * ND, *S = yv + CX * ND, *g = S + TM_S;
+    double *uq = g + DIM * CX * NQ;
+    const MeshDesc &m = a.mesh;
+    const int nb = min(NB, m.ne - e0);
+    const bool lim = a.lim != 0.0;
+    load_tab(st, a.tab);
+    gather_elem(uu, a.u, DIM, m, e0, nb);
+    __syncthreads();
+    grad_ref<DIM, D, Q, CX>(uu, g, S, st + oB, st + oG);
+    if (lim) interp<DIM, D, Q, CX>(uu, uq, S, st + oB);
+    for (int k = threadIdx.x; k < nb * NQ; k += blockDim.x) {
+      const int b = k / NQ, q = k % NQ;
+      double Z[NR];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) Z[c * DIM + l] = g[(l * CX + b * DIM + c) * NQ + q];
+      const double *He = a.pa + (size_t)(e0 + b) * NH2 * NQ + q;
+      double y[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) y[r] = 0.0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int s = r; s < NR; ++s) {
+          const double h = He[(size_t)hidx(r, s) * NQ];
+          y[r] = fma(h, Z[s], y[r]);
+          if (s != r) y[s] = fma(h, Z[r], y[s]);
+        }
+#pragma unroll
+      for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int n = 0; n < DIM; ++n) g[(n * CX + b * DIM + c) * NQ + q] = y[c * DIM + n];
+      if (lim) {
+        double w, iw;
+        qweight(st, q, w, iw);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) uq[(b * DIM + c) * NQ + q] *= 2.0 * a.lim * w * a.detW;
+      }
+    }
+    __syncthreads();
+    grad_ref_t<DIM, D, Q, CX>(g, yv, S, st + oBt, st + oGt);
+    if (lim) interp<DIM, Q, D, CX>(uq, uu, S, st + oBt);
+    for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x)
+      a.evec[(size_t)e0 * DIM * ND + k] = lim ? yv[k] + uu[k] : yv[k];
+  }
+
   // ===== remap phase (Section 3.5): one stage on the mesh x(tau) = x0 + tau u ====
   // Per element and qpoint of x(tau): mq = omega detJ (the mass data of M(tau)) and
   // the advection data adv_l = omega detJ (J^-1 u)_l = omega (adj(J) u)_l, kept in
@@ -1924,6 +2029,10 @@ __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_stiff_setup(Stif
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_stiff(StiffArgs a) { Family<DIM, P, Q>::body_stiff(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q, int MODE>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_tmop(TmopArgs a) { Family<DIM, P, Q>::template body_tmop<MODE>(a, blockIdx.x * Family<DIM, P, Q>::NB); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_tmop(TmopArgs a) {
+  if constexpr (MODE == 4) Family<DIM, P, Q>::body_tmop_pa_setup(a, blockIdx.x * Family<DIM, P, Q>::NB);
+  else if constexpr (MODE == 5) Family<DIM, P, Q>::body_tmop_pa_apply(a, blockIdx.x * Family<DIM, P, Q>::NB);
+  else Family<DIM, P, Q>::template body_tmop<MODE>(a, blockIdx.x * Family<DIM, P, Q>::NB);
+}
 
 }  // namespace lh

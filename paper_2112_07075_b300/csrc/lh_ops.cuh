@@ -147,7 +147,9 @@ struct OpsBuilder {
       case 0: k_tmop<DIM, P, Q, 0><<<grid, F::THREADS, F::tmop_smem(0), s>>>(a); break;
       case 1: k_tmop<DIM, P, Q, 1><<<grid, F::THREADS, F::tmop_smem(1), s>>>(a); break;
       case 2: k_tmop<DIM, P, Q, 2><<<grid, F::THREADS, F::tmop_smem(2), s>>>(a); break;
-      default: k_tmop<DIM, P, Q, 3><<<grid, F::THREADS, F::tmop_smem(3), s>>>(a); break;
+      case 3: k_tmop<DIM, P, Q, 3><<<grid, F::THREADS, F::tmop_smem(3), s>>>(a); break;
+      case 4: k_tmop<DIM, P, Q, 4><<<grid, F::THREADS, F::tmop_smem(0), s>>>(a); break;
+      default: k_tmop<DIM, P, Q, 5><<<grid, F::THREADS, F::tmop_smem(0), s>>>(a); break;
     }
   }
   static void node_table(const MeshDesc &m, int *tab, int grid, int threads, cudaStream_t s) {
@@ -168,9 +170,10 @@ struct OpsBuilder {
                             F::remap_smem(), (void *)k_remap<DIM, P, Q>, &remap, &remap_nodes,
                             F::stiff_setup_smem(), F::stiff_smem(), (void *)k_stiff_setup<DIM, P, Q>,
                             (void *)k_stiff<DIM, P, Q>, &stiff_setup, &stiff,
-                            {F::tmop_smem(0), F::tmop_smem(1), F::tmop_smem(2), F::tmop_smem(3)},
+                            {F::tmop_smem(0), F::tmop_smem(1), F::tmop_smem(2), F::tmop_smem(3), F::tmop_smem(0),
+                             F::tmop_smem(0)},
                             {(void *)k_tmop<DIM, P, Q, 0>, (void *)k_tmop<DIM, P, Q, 1>, (void *)k_tmop<DIM, P, Q, 2>,
-                             (void *)k_tmop<DIM, P, Q, 3>},
+                             (void *)k_tmop<DIM, P, Q, 3>, (void *)k_tmop<DIM, P, Q, 4>, (void *)k_tmop<DIM, P, Q, 5>},
                             &tmop, &node_table};
     return &ops;
   }

@@ -33,7 +33,7 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc",
             "lh_remap_velocity", "lh_remap_apply", "lh_stiffness_setup", "lh_stiffness_mult", "lh_laplacian",
             "lh_tmop_objective", "lh_tmop_gradient", "lh_tmop_hessian_mult", "lh_tmop_hessian_diag",
-            "lh_set_dt_control"]
+            "lh_set_dt_control", "lh_tmop_workspace_size", "lh_tmop_hessian_setup", "lh_tmop_hessian_mult_pa"]
 
 
 class LhParams(ctypes.Structure):
@@ -130,6 +130,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_tmop_gradient": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP, VP]),
         "lh_tmop_hessian_mult": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP, VP]),
         "lh_tmop_hessian_diag": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP]),
+        "lh_tmop_workspace_size": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "lh_tmop_hessian_setup": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP]),
+        "lh_tmop_hessian_mult_pa": (I, [P, ctypes.POINTER(LhTmopParams), VP, VP, VP, VP]),
         "lh_timing_read": (I, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]),
         "lh_learn_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_double)]),
@@ -337,6 +340,21 @@ class Context:
     def tmop_hessian_diag(self, x, diag, h, gamma=0.0, dlim=1.0):
         self._check(self.lib.lh_tmop_hessian_diag(self.h, self._tmop_prm(h, gamma, dlim), _ptr(x), _ptr(diag),
                                                   _stream()))
+
+    def tmop_workspace(self):
+        """A DEVICE float64 workspace for the partially assembled TMOP Hessian."""
+        import torch
+        n = ctypes.c_int64(0)
+        self._check(self.lib.lh_tmop_workspace_size(self.h, ctypes.byref(n)))
+        return torch.empty(int(n.value), dtype=torch.float64, device=self.device)
+
+    def tmop_hessian_setup(self, x, work, h, gamma=0.0, dlim=1.0):
+        self._check(self.lib.lh_tmop_hessian_setup(self.h, self._tmop_prm(h, gamma, dlim), _ptr(x), _ptr(work),
+                                                   _stream()))
+
+    def tmop_hessian_mult_pa(self, work, u, y, h, gamma=0.0, dlim=1.0):
+        self._check(self.lib.lh_tmop_hessian_mult_pa(self.h, self._tmop_prm(h, gamma, dlim), _ptr(work), _ptr(u),
+                                                     _ptr(y), _stream()))
 
     def sync_status(self) -> int:
         return int(self.lib.lh_sync_status(self.h))

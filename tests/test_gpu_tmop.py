@@ -166,3 +166,24 @@ def test_full_size_lagrangian_mesh_on_samples():
         scale = max(np.max(np.abs(Hu)), 1e-30)
         assert np.max(np.abs(yg[:, gnode] - Hu)) <= 1e-10 * max(scale, np.max(np.abs(yg))), gnode
         assert np.max(np.abs(dgg[:, gnode] - Hd)) <= 1e-12 * np.max(np.abs(Hd)), gnode
+
+
+@pytest.mark.parametrize("dim,p,q1,n", FAMILIES)
+def test_partially_assembled_hessian_matches_oracle(dim, p, q1, n):
+    ctx, m, tm, x0, h = _case(dim, p, q1, n, 0.3)
+    x = m.x0
+    kw = dict(h=h, gamma=0.3, dlim=0.5 * h)
+    work = ctx.tmop_workspace()
+    assert work.numel() == m.NE * (dim * dim) * (dim * dim + 1) // 2 * q1 ** dim
+    ctx.tmop_hessian_setup(_dev(x), work, **kw)
+    H = tm.hessian(x)
+    for seed in (61, 62):                     # several products from one setup
+        u = inputs.uniform(seed, (dim, m.NH1), -1.0, 1.0)
+        y, ymf = ctx.h1_vector(), ctx.h1_vector()
+        ctx.tmop_hessian_mult_pa(work, _dev(u), y, **kw)
+        ctx.tmop_hessian_mult(_dev(x), _dev(u), ymf, **kw)
+        ref = (H @ u.ravel()).reshape(dim, m.NH1)
+        scale = (abs(H) @ abs(u).ravel()).max()
+        assert np.max(np.abs(_np(y) - ref)) <= 1e-12 * scale
+        assert np.max(np.abs(_np(y) - _np(ymf))) <= 1e-12 * scale
+    assert ctx.sync_status() == 0
