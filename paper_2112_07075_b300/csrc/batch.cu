@@ -35,6 +35,7 @@ struct BProb {      // per-problem record used by node kernels and the batched s
   MeshDesc m;
   int order, n_nitems, first_nitem, source;
   const double *tab, *mq, *invdiag, *dt;
+  const int *ncopy;                      // the problem's node-copy table [N_H1][4]
   double *evec, *r, *p, *ap, *a, *rhs;   // a = acceleration (CG solution, warm start)
   double *x, *v, *e, *xh, *vh, *vb;
   lh_step_info *info;
@@ -104,6 +105,14 @@ __global__ void __launch_bounds__(kThreads) k_b_force_t(const ForceTArgs *args, 
   }
 }
 
+// Copies of node g from the problem's node-copy table (the -1 padding comes last, so
+// the first n entries are the copies in the fixed gather order); returns n.
+__device__ __forceinline__ int table_copies(const int *__restrict__ tab, int g, int (&off)[4]) {
+  const int4 t = __ldg(reinterpret_cast<const int4 *>(tab + (size_t)g * 4));
+  off[0] = t.x; off[1] = t.y; off[2] = t.z; off[3] = t.w;
+  return (t.x >= 0) + (t.y >= 0) + (t.z >= 0) + (t.w >= 0);
+}
+
 // ---- batched node kernels --------------------------------------------------
 // rhs = -(F.1) gathered from the E-vector, zero on constrained DOFs.
 __global__ void k_b_rhs(const BProb *probs, const ItemN *items, int nitems) {
@@ -115,7 +124,7 @@ __global__ void k_b_rhs(const BProb *probs, const ItemN *items, int nitems) {
       dispatch_order(pb.order, [&](auto P) {
         constexpr int D = decltype(P)::value + 1, ND = D * D;
         int off[4];
-        const int n = node_copies<2, D>(pb.m, g, 2, off);
+        const int n = table_copies(pb.ncopy, g, off);
         for (int c = 0; c < 2; ++c) {
           const int k = c * pb.m.nh1 + g;
           double s = pb.evec[off[0] + c * ND];
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
       dispatch_order(pb.order, [&](auto P) {
         constexpr int D = decltype(P)::value + 1, ND = D * D;
         int off[4];
-        const int n = node_copies<2, D>(pb.m, g, 2, off);
+        const int n = table_copies(pb.ncopy, g, off);
         for (int c = 0; c < 2; ++c) {
           const int k = c * pb.m.nh1 + g;
           const double idg = pb.invdiag[k];
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
         dispatch_order(pb.order, [&](auto P) {
           constexpr int D = decltype(P)::value + 1, ND = D * D;
           int off[4];
-          const int n = node_copies<2, D>(pb.m, g, 2, off);
+          const int n = table_copies(pb.ncopy, g, off);
           for (int c = 0; c < 2; ++c) {
             const int k = c * pb.m.nh1 + g;
             const double idg = pb.invdiag[k];
@@ -569,6 +578,7 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
     p.tab = c->tab;
     p.mq = c->mq;
     p.invdiag = c->invdiag;
+    p.ncopy = c->ncopy;
     p.evec = c->evec;
     p.r = c->r;
     p.p = c->pv;
