@@ -1027,8 +1027,9 @@ lh_status lh_laplacian(lh_ctx *ctx, const double *v, double *lap, double rel_tol
 // ---------------------------------------------------------------------------
 // Mesh optimisation (TMOP, Sections 2.2 and 3.4)
 // ---------------------------------------------------------------------------
-static lh_status tmop_args(lh_ctx *c, const lh_tmop_params *prm, const double *x, TmopArgs &a) {
-  if (!prm || !x) return fail(c, LH_ERR_ARG, "null pointer");
+// x may be NULL only for calls that do not read positions (need_x = false).
+static lh_status tmop_args(lh_ctx *c, const lh_tmop_params *prm, const double *x, TmopArgs &a, bool need_x = true) {
+  if (!prm || (need_x && !x)) return fail(c, LH_ERR_ARG, "null pointer");
   if (!(prm->target_size > 0.0)) return fail(c, LH_ERR_ARG, "target_size must be > 0");
   if (!(prm->lim_weight >= 0.0)) return fail(c, LH_ERR_ARG, "lim_weight must be >= 0");
   if (prm->lim_weight > 0.0 && !(prm->lim_dist > 0.0)) return fail(c, LH_ERR_ARG, "lim_dist must be > 0");
@@ -1116,11 +1117,9 @@ lh_status lh_tmop_hessian_setup(lh_ctx *ctx, const lh_tmop_params *prm, const do
 lh_status lh_tmop_hessian_mult_pa(lh_ctx *ctx, const lh_tmop_params *prm, const double *work, const double *u,
                                   double *y, lh_stream_t stream) {
   if (!ctx || !work || !u || !y) return ctx ? fail(ctx, LH_ERR_ARG, "null pointer") : LH_ERR_ARG;
-  if (!prm) return fail(ctx, LH_ERR_ARG, "null pointer");
   if (y == u || y == work) return fail(ctx, LH_ERR_ARG, "y must not alias u or the workspace");
   TmopArgs a;
-  if (lh_status st = tmop_args(ctx, prm, u, a)) return st;   // x is not read by the action
-  a.x = nullptr;
+  if (lh_status st = tmop_args(ctx, prm, nullptr, a, false)) return st;   // the action reads no positions
   a.u = u;
   a.pa = const_cast<double *>(work);
   return tmop_vector(ctx, 5, a, y, (cudaStream_t)stream);
