@@ -333,6 +333,7 @@ static lh_status setup_impl(lh_ctx *c, const lh_params *prm, const double *rho0_
       {(double **)&c->mq32, nf * (NE * NQ + 1) / 2},  {(double **)&c->invdiag32, nf * (NV + 1) / 2},
       {(double **)&c->r32, nf * (NV + 1) / 2},        {(double **)&c->p32, nf * (NV + 1) / 2},
       {(double **)&c->ap32, nf * (NV + 1) / 2},       {(double **)&c->d32, nf * (NV + 1) / 2},
+      {(double **)&c->z32, nf * (NV + 1) / 2},
       {(double **)&c->evec32, nf * (NE * dim * c->nd + 1) / 2},
       {(double **)&c->kimg, tcf ? (o.tc_img_bytes + 7) / 8 : 0}};
   size_t bytes = 0;
@@ -588,6 +589,7 @@ static lh_status cg_launch(lh_ctx *c, const double *b, double *x, double tol, in
     a.ap32 = c->ap32;
     a.d32 = c->d32;
     a.evec32 = c->evec32;
+    a.z32 = c->z32;
     a.bar = c->bar;
     a.status = c->dstatus;
     a.info = info;

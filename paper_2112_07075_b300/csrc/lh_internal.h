@@ -87,6 +87,7 @@ struct CgIrArgs {
   const float *mq32, *invdiag32;
   double *x, *evec, *partials;
   float *r32, *p32, *ap32, *d32, *evec32;
+  float *z32;         // invdiag32 * r32, kept beside r32 by the inner solver
   void *bar;
   int *status;
   lh_cg_info *info;
@@ -261,7 +262,7 @@ struct lh_ctx {
   float *stiff_mq32 = nullptr, *stiff_inv32 = nullptr;   // precision form only
   bool stiff_ready = false;
   float *mq32 = nullptr, *invdiag32 = nullptr, *r32 = nullptr, *p32 = nullptr, *ap32 = nullptr, *d32 = nullptr,
-        *evec32 = nullptr;
+        *evec32 = nullptr, *z32 = nullptr;
   int grid_cg_ir = 0, grid_cg_tc = 0;
   unsigned short *kimg = nullptr;   // tensor-core form: BF16 image of the interpolation matrix
   unsigned int *counter = nullptr;

@@ -702,11 +702,11 @@ struct Family {
   template <int MODE, typename T>
   static __device__ __forceinline__ T dir_value(int gi, const T *__restrict__ idv, const T *x, const T *r,
                                                 const T *q, const T *p, T alpha, T beta) {
+    if (MODE == 4) return fma(beta, p[gi], x[gi]);   // x holds z = invdiag r
     const T idg = idv[gi];
     if (MODE == 0) return idg != (T)0 ? x[gi] : (T)0;
     if (MODE == 1) return idg * r[gi];
     if (MODE == 3) return fma(beta, p[gi], idg * r[gi]);
-    if (MODE == 4) return fma(beta, p[gi], x[gi]);   // x holds z = invdiag r
     return fma(beta, p[gi], idg * fma(-alpha, q[gi], r[gi]));
   }
 
@@ -769,12 +769,82 @@ struct Family {
                                                         float beta, float *evec, float &dot) {
     const int nbatch = (m.ne + NBF - 1) / NBF;
     constexpr int MQT = (CXF * NQ + TC - 1) / TC;   // mass-data values per thread (blockDim == TC)
+    constexpr bool kPrefetch = MQT <= 16;
+    if constexpr (P >= 4) {
+      // high orders (one CTA per SM, many batches per CTA): software-pipelined gather.
+      // The next batch's values are loaded into registers right after this batch's
+      // have been stored, so their latency overlaps this batch's contractions.
+      constexpr int GV = (CXF * ND + TC - 1) / TC;
+      float nxt[GV];
+      auto gather_regs = [&](int nbg) {
+#pragma unroll
+        for (int v = 0; v < GV; ++v) {
+          const int k = threadIdx.x + v * TC;
+          const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+          nxt[v] = (k < CXF * ND && b < nbg)
+                       ? dir_value<MODE, float>(c * m.nh1 + eb[b] + h1_local<DIM, D>(m, i), idv, x, r, q, p, alpha,
+                                                beta)
+                       : 0.0f;
+        }
+      };
+      int bt = blockIdx.x;
+      if (bt < nbatch) {
+        const int nb = min(NBF, m.ne - bt * NBF);
+        if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, bt * NBF + threadIdx.x);
+        __syncthreads();
+        gather_regs(nb);
+      }
+      for (; bt < nbatch; bt += gridDim.x) {
+        const int e0 = bt * NBF, nb = min(NBF, m.ne - e0);
+        float mqr[kPrefetch ? MQT : 1];
+        if constexpr (kPrefetch) {
+#pragma unroll
+          for (int j = 0; j < MQT; ++j) {
+            const int k = threadIdx.x + j * TC;
+            const int qq = k % NQ, b = (k / NQ) / DIM;
+            mqr[j] = (k < CXF * NQ && b < nb) ? mq[(size_t)(e0 + b) * NQ + qq] : 0.0f;
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < GV; ++v) {
+          const int k = threadIdx.x + v * TC;
+          if (k < CXF * ND) u[k] = nxt[v];
+        }
+        // base nodes of the next batch (the previous readers of eb are past the last barrier)
+        const int btn = bt + gridDim.x;
+        const int nbn = btn < nbatch ? min(NBF, m.ne - btn * NBF) : 0;
+        if (threadIdx.x < nbn) eb[threadIdx.x] = h1_base<DIM, D>(m, btn * NBF + threadIdx.x);
+        __syncthreads();
+        if (nbn > 0) gather_regs(nbn);
+        interp_p<DIM, D, Q, CXF>(u, uq, S, tb);
+        if constexpr (kPrefetch) {
+#pragma unroll
+          for (int j = 0; j < MQT; ++j) {
+            const int k = threadIdx.x + j * TC;
+            if (k < CXF * NQ) uq[k] *= mqr[j];
+          }
+        } else {
+          for (int k = threadIdx.x; k < CXF * NQ; k += blockDim.x) {
+            const int qq = k % NQ, b = (k / NQ) / DIM;
+            uq[k] *= b < nb ? mq[(size_t)(e0 + b) * NQ + qq] : 0.0f;
+          }
+        }
+        __syncthreads();
+        interp_p<DIM, Q, D, CXF>(uq, y, S, tbt);
+        for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) {
+          const float yk = y[k];
+          evec[(size_t)e0 * DIM * ND + k] = yk;
+          dot = fmaf(u[k], yk, dot);
+        }
+        __syncthreads();
+      }
+      return;
+    }
     for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
       const int e0 = bt * NBF, nb = min(NBF, m.ne - e0);
       // issue this batch's mass-data loads first: they are needed only after the
       // first contraction stages, so their latency overlaps the gather and stages
       // (only while the prefetch array is small: more registers would cost occupancy)
-      constexpr bool kPrefetch = MQT <= 16;
       float mqr[kPrefetch ? MQT : 1];
       if constexpr (kPrefetch) {
 #pragma unroll
@@ -786,11 +856,26 @@ struct Family {
       }
       if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, e0 + threadIdx.x);
       __syncthreads();
-      for (int k = threadIdx.x; k < CXF * ND; k += blockDim.x) {
-        const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
-        float val = 0.0f;
-        if (b < nb) val = dir_value<MODE, float>(c * m.nh1 + eb[b] + h1_local<DIM, D>(m, i), idv, x, r, q, p, alpha, beta);
-        u[k] = val;
+      // gather: GU values per pass, every global load of the pass issued before the
+      // shared-memory stores (a store through a generic pointer would otherwise hold
+      // the next value's loads back)
+      constexpr int GU = 4;
+      for (int k0 = threadIdx.x; k0 < CXF * ND; k0 += GU * blockDim.x) {
+        float val[GU];
+#pragma unroll
+        for (int uix = 0; uix < GU; ++uix) {
+          const int k = k0 + uix * blockDim.x;
+          const int i = k % ND, bc = k / ND, c = bc % DIM, b = bc / DIM;
+          val[uix] = (k < CXF * ND && b < nb)
+                         ? dir_value<MODE, float>(c * m.nh1 + eb[b] + h1_local<DIM, D>(m, i), idv, x, r, q, p, alpha,
+                                                  beta)
+                         : 0.0f;
+        }
+#pragma unroll
+        for (int uix = 0; uix < GU; ++uix) {
+          const int k = k0 + uix * blockDim.x;
+          if (k < CXF * ND) u[k] = val[uix];
+        }
       }
       __syncthreads();
       interp_p<DIM, D, Q, CXF>(u, uq, S, tb);
@@ -1002,7 +1087,7 @@ struct Family {
           __syncthreads();
         },
         [&](float beta, float &pq) {
-          sweep_matvec_f<3>(a.mesh, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.d32, a.r32, a.ap32,
+          sweep_matvec_f<4>(a.mesh, s_eb, tb, tbt, uf, Sf, uqf, yf, a.mq32, a.invdiag32, a.z32, a.r32, a.ap32,
                             a.p32, 0.0f, beta, a.evec32, pq);
           return true;
         });
@@ -1099,6 +1184,7 @@ struct Family {
               a.x[k] = 0.0;
             }
             a.r32[k] = rf;
+            a.z32[k] = rf * a.invdiag32[k];
             a.d32[k] = 0.0f;
             a.p32[k] = 0.0f;
             a.ap32[k] = 0.0f;
@@ -1176,51 +1262,69 @@ struct Family {
            // r.r and r.z; one (node, component) per work item, copies through the
            // node-copy table, every load issued first
           float acc[5] = {0, 0, 0, 0, 0};
-          // U work items per pass, all of their loads in flight together. High orders
-          // (p >= 3) run one large CTA per SM and many items per thread: overlap 4;
-          // low orders keep the register count that allows two CTAs per SM.
-          constexpr int U = P >= 3 ? 4 : 1;
-          const int nvk = DIM * nh1;
-          for (int k0 = gtid; k0 < nvk; k0 += U * gstride) {
-            int kk[U], cc[U], off[U][1 << DIM];
-            float idg[U], pv[U], rv[U], dv[U], ev[U][1 << DIM];
+          if constexpr (P >= 3) {
+            // high orders: one node per work item, its table row read once and the
+            // loads of all DIM components in flight together (FP32 leaves the registers)
+            for (int g = gtid; g < nh1; g += gstride) {
+              int off[1 << DIM];
+              node_table_row<DIM>(a.ncopy, g, off);
+              float idg[DIM], pv[DIM], rv[DIM], dv[DIM], ev[DIM][1 << DIM];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const int k = k0 + u * gstride;
-              kk[u] = k;
-              const bool ok = k < nvk;
-              const int kc = ok ? k : 0;
-              cc[u] = DIM == 2 ? (kc >= nh1 ? 1 : 0) : (kc >= 2 * nh1 ? 2 : (kc >= nh1 ? 1 : 0));
-              node_table_row<DIM>(a.ncopy, kc - cc[u] * nh1, off[u]);
-              if (!ok) {
+              for (int c = 0; c < DIM; ++c) {
+                const int k = c * nh1 + g;
+                idg[c] = __ldg(a.invdiag32 + k);
+                pv[c] = a.p32[k];
+                rv[c] = a.r32[k];
+                dv[c] = a.d32[k];
 #pragma unroll
-                for (int j = 0; j < (1 << DIM); ++j) off[u][j] = -1;
+                for (int j = 0; j < (1 << DIM); ++j) ev[c][j] = off[j] >= 0 ? a.evec32[off[j] + c * ND] : 0.0f;
               }
-              idg[u] = ok ? __ldg(a.invdiag32 + kc) : 0.0f;
-              pv[u] = a.p32[kc];
-              rv[u] = a.r32[kc];
-              dv[u] = a.d32[kc];
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) {
+                float qv = ev[c][0];
+#pragma unroll
+                for (int j = 1; j < (1 << DIM); ++j)
+                  if (off[j] >= 0) qv += ev[c][j];
+                if (idg[c] != 0.0f) {   // constrained DOFs keep p = r = d = 0
+                  const int k = c * nh1 + g;
+                  const float pn = fmaf(beta, pv[c], idg[c] * rv[c]);
+                  const float r2 = fmaf(-alpha, qv, rv[c]);
+                  const float z2 = r2 * idg[c];
+                  a.p32[k] = pn;
+                  a.d32[k] = fmaf(alpha, pn, dv[c]);
+                  a.r32[k] = r2;
+                  a.z32[k] = z2;
+                  acc[0] = fmaf(r2, r2, acc[0]);
+                  acc[1] = fmaf(z2, r2, acc[1]);
+                }
+              }
             }
+          } else {
+            // low orders: one (node, component) per work item (keeps the register count
+            // that allows two CTAs per SM)
+            for (int k = gtid; k < DIM * nh1; k += gstride) {
+              const int c = DIM == 2 ? (k >= nh1 ? 1 : 0) : (k >= 2 * nh1 ? 2 : (k >= nh1 ? 1 : 0));
+              int off[1 << DIM];
+              node_table_row<DIM>(a.ncopy, k - c * nh1, off);
+              const float idg = __ldg(a.invdiag32 + k);
+              const float pv = a.p32[k], rv = a.r32[k], dv = a.d32[k];
+              float ev[1 << DIM];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-              for (int j = 0; j < (1 << DIM); ++j)
-                ev[u][j] = off[u][j] >= 0 ? a.evec32[off[u][j] + cc[u] * ND] : 0.0f;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-              float qv = ev[u][0];
+              for (int j = 0; j < (1 << DIM); ++j) ev[j] = off[j] >= 0 ? a.evec32[off[j] + c * ND] : 0.0f;
+              float qv = ev[0];
 #pragma unroll
               for (int j = 1; j < (1 << DIM); ++j)
-                if (off[u][j] >= 0) qv += ev[u][j];
-              if (idg[u] != 0.0f) {   // constrained DOFs (and items past the end) keep p = r = d
-                const int k = kk[u];
-                const float pn = fmaf(beta, pv[u], idg[u] * rv[u]);
-                const float r2 = fmaf(-alpha, qv, rv[u]);
+                if (off[j] >= 0) qv += ev[j];
+              if (idg != 0.0f) {   // constrained DOFs keep p = r = d = 0
+                const float pn = fmaf(beta, pv, idg * rv);
+                const float r2 = fmaf(-alpha, qv, rv);
+                const float z2 = r2 * idg;
                 a.p32[k] = pn;
-                a.d32[k] = fmaf(alpha, pn, dv[u]);
+                a.d32[k] = fmaf(alpha, pn, dv);
                 a.r32[k] = r2;
+                a.z32[k] = z2;
                 acc[0] = fmaf(r2, r2, acc[0]);
-                acc[1] = fmaf(r2 * idg[u], r2, acc[1]);
+                acc[1] = fmaf(z2, r2, acc[1]);
               }
             }
           }

@@ -191,11 +191,11 @@ struct TcMass {
               const int k = lane + 32 * jj;
               const int el = k < seg ? k / D : 0, ix = k < seg ? k - (k / D) * D : 0;
               const int gi = goff + s_base[el] + ix;
-              ld0[jj] = __ldg(a.invdiag32 + gi);
               if constexpr (MODE == 0) {
+                ld0[jj] = __ldg(a.invdiag32 + gi);
                 ld1[jj] = a.d32[gi];
-              } else {
-                ld1[jj] = a.r32[gi];
+              } else {   // z = invdiag r is kept beside r by the node sweeps
+                ld1[jj] = a.z32[gi];
                 ld2[jj] = a.p32[gi];
               }
             }
@@ -205,7 +205,7 @@ struct TcMass {
               const int r = r_c + 3 * (k / D);
               float val;
               if constexpr (MODE == 0) val = ld0[jj] != 0.0f ? ld1[jj] : 0.0f;   // masked x
-              else val = fmaf(beta, ld2[jj], ld0[jj] * ld1[jj]);                  // invdiag r + beta p
+              else val = fmaf(beta, ld2[jj], ld1[jj]);                            // z + beta p
               v[jj] = (k < seg && r >= 0 && r < L::ROWS) ? val : 0.0f;
             }
           }
