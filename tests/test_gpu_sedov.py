@@ -29,13 +29,17 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("dim,n,p,q1,jit,attempts", [(2, 8, 2, 4, 0.0, 16), (3, 4, 2, 4, 0.0, 12),
-                                                     (2, 6, 3, 6, 0.1, 12), (3, 3, 3, 6, 0.05, 8)])
-def test_sedov_controlled_run_matches_oracle(dim, n, p, q1, jit, attempts):
+@pytest.mark.parametrize("dim,n,p,q1,jit,attempts,precision",
+                         [(2, 8, 2, 4, 0.0, 16, "fp64"), (3, 4, 2, 4, 0.0, 12, "fp64"),
+                          (2, 6, 3, 6, 0.1, 12, "fp64"), (3, 3, 3, 6, 0.05, 8, "fp64"),
+                          (2, 8, 2, 4, 0.0, 16, "fp32_ir"), (3, 3, 3, 6, 0.05, 8, "bf16tc_ir")])
+def test_sedov_controlled_run_matches_oracle(dim, n, p, q1, jit, attempts, precision):
+    """The precision forms' solves stop at the same FP64 residual criterion, so their
+    decisions and fields are held to the same bars as the FP64 path."""
     from paper_2112_07075_b300.lh import Context
     V = inputs.box_vertices(dim, n, jitter=jit, seed=2)
     hy = Hydro(Params(dim=dim, n=n, order=p, q1=q1, vertices=V, gamma=1.4, cfl=0.5))
-    ctx = Context(dim, n, V, p, q1, gamma=1.4, cfl=0.5)
+    ctx = Context(dim, n, V, p, q1, gamma=1.4, cfl=0.5, precision=precision)
     ctx.set_dt_control(True)
     xo, vo, eo = hy.initial_state("sedov")
     xg, vg, eg = ctx.init_state("sedov")
