@@ -217,6 +217,26 @@ def test_energy_conservation_and_determinism():
     assert abs(E1 - E0) < 1e-11 * E0                 # CG tolerance 1e-12 bounds the drift
 
 
+
+@pytest.mark.parametrize("n", [24, 28])
+def test_full_size_runs_are_bit_identical(n):
+    """Benchmark-size meshes (every solver block sweeps several element batches, the
+    grid barriers and block sums run at full width): two runs from the same state
+    give bit-identical fields, iteration counts and times."""
+    V = inputs.box_vertices(3, n)
+    runs = []
+    for _ in range(2):
+        ctx = _ctx(3, n, 2, 4, V)
+        x, v, e = ctx.init_state()
+        info = ctx.new_step_info(0.0, 1.0)
+        for _ in range(3):
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+        si = ctx.read_step_info(info)
+        assert si.status == 0
+        runs.append((_np(x), _np(v), _np(e), si.cg_iters_total, si.t))
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
 def test_inverted_element_is_reported():
     V = inputs.box_vertices(2, 2)
     ctx = _ctx(2, 2, 1, 2, V)
