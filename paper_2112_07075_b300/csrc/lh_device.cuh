@@ -278,11 +278,21 @@ __device__ __forceinline__ double block_max(double v, double *red) {
   return v;
 }
 
-// Sum of n partials in a fixed order, computed by one warp (result in every lane).
+// Sum of n partials in a fixed order, computed by one warp (result in every lane):
+// lane l adds p[l], p[l + 32], ... in turn, then the lanes are summed. The loads
+// are issued eight at a time, ahead of the additions, which keep that order.
 __device__ __forceinline__ double warp_sum_partials(const double *p, int n) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int i = lane; i < n; i += 32) s += p[i];
+  int i = lane;
+  for (; i + 7 * 32 < n; i += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = p[i + 32 * j];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += v[j];
+  }
+  for (; i < n; i += 32) s += p[i];
   return warp_sum(s);
 }
 

@@ -89,6 +89,47 @@ __device__ __forceinline__ int node_copies(const MeshDesc &m, int g, int C, int 
   return n;
 }
 
+// Offsets e*C*ND + i of node g's element copies, computed from the node's grid
+// coordinates (no table read): position j = (a*2 + b)*2 + k picks the z, y, x
+// owner (2D: j = b*2 + k); -1 where that axis has a single owner. Position 0 is
+// always a copy, and the valid positions come in the order of node_copies (and of
+// the node-copy table), so sums over the copies in position order are the same.
+template <int DIM, int D>
+__device__ __forceinline__ void node_offsets(const MeshDesc &m, int g, int C, int (&off)[1 << DIM]) {
+  constexpr int P = D - 1, ND = ipow<D, DIM>::value;
+  // along one axis: the first owner (element e-1 at local index P when the node
+  // sits on an element boundary other than the first, else element e at index i)
+  // and the second (element e at index 0) if the boundary is interior
+  auto axis = [](int gc, int nel, int se, int si, int &o0, int &o1) {
+    const int e = gc / P, i = gc - e * P;
+    const bool lo = i == 0 && e > 0;
+    o0 = (lo ? e - 1 : e) * se + (lo ? P : i) * si;
+    o1 = lo && e < nel ? e * se : -1;
+  };
+  const int gx = g % m.n1x, t = g / m.n1x;
+  int x0, x1, y0, y1;
+  axis(gx, m.nx, C * ND, 1, x0, x1);
+  if constexpr (DIM == 2) {
+    axis(t, m.ny, m.nx * C * ND, D, y0, y1);
+    off[0] = x0 + y0;
+    off[1] = x1 >= 0 ? x1 + y0 : -1;
+    off[2] = y1 >= 0 ? x0 + y1 : -1;
+    off[3] = x1 >= 0 && y1 >= 0 ? x1 + y1 : -1;
+  } else {
+    int z0, z1;
+    axis(t % m.n1y, m.ny, m.nx * C * ND, D, y0, y1);
+    axis(t / m.n1y, m.nz, m.nx * m.ny * C * ND, D * D, z0, z1);
+    const int xs[2] = {x0, x1}, ys[2] = {y0, y1}, zs[2] = {z0, z1};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          off[(a * 2 + b) * 2 + k] = xs[k] >= 0 && ys[b] >= 0 && zs[a] >= 0 ? xs[k] + ys[b] + zs[a] : -1;
+  }
+}
+
 // Row g of the node-copy table (offsets e*DIM*ND + i of node g's copies, -1 padded).
 template <int DIM>
 __device__ __forceinline__ void node_table_row(const int *__restrict__ tab, int g, int (&off)[1 << DIM]) {
@@ -793,6 +834,9 @@ struct Family {
         if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, bt * NBF + threadIdx.x);
         __syncthreads();
         gather_regs(nb);
+        // every warp has read eb before the loop overwrites it with the next batch's
+        // base nodes (the loads it issued stay in flight across the barrier)
+        __syncthreads();
       }
       for (; bt < nbatch; bt += gridDim.x) {
         const int e0 = bt * NBF, nb = min(NBF, m.ne - e0);
@@ -810,7 +854,7 @@ struct Family {
           const int k = threadIdx.x + v * TC;
           if (k < CXF * ND) u[k] = nxt[v];
         }
-        // base nodes of the next batch (the previous readers of eb are past the last barrier)
+        // base nodes of the next batch (every earlier reader of eb is past a barrier)
         const int btn = bt + gridDim.x;
         const int nbn = btn < nbatch ? min(NBF, m.ne - btn * NBF) : 0;
         if (threadIdx.x < nbn) eb[threadIdx.x] = h1_base<DIM, D>(m, btn * NBF + threadIdx.x);
@@ -1049,10 +1093,11 @@ struct Family {
         }
       }
       if (!sync()) { finish(it, kStatusTimeout, rr, bb); return; }
-      if (threadIdx.x < 32) {
-        const double v1 = warp_sum_partials(a.partials + (size_t)1 * G, G);
-        const double v2 = warp_sum_partials(a.partials + (size_t)2 * G, G);
-        if (threadIdx.x == 0) { s_sc[1] = v1; s_sc[2] = v2; }
+      static_assert(TC >= 64, "the solver's final sums take two warps");
+      if (threadIdx.x < 64) {   // r.r on warp 0, r.z on warp 1, side by side
+        const int w = threadIdx.x >> 5;
+        const double v = warp_sum_partials(a.partials + (size_t)(1 + w) * G, G);
+        if ((threadIdx.x & 31) == 0) s_sc[1 + w] = v;
       }
       __syncthreads();
       rr = s_sc[1];
@@ -1263,11 +1308,13 @@ struct Family {
            // node-copy table, every load issued first
           float acc[5] = {0, 0, 0, 0, 0};
           if constexpr (P >= 3) {
-            // high orders: one node per work item, its table row read once and the
-            // loads of all DIM components in flight together (FP32 leaves the registers)
+            // high orders: one node per work item, the loads of all DIM components in
+            // flight together (FP32 leaves the registers)
             for (int g = gtid; g < nh1; g += gstride) {
+              // copy offsets from the node's coordinates: no table traffic and one
+              // memory round trip per node (this sweep is bound by HBM at large sizes)
               int off[1 << DIM];
-              node_table_row<DIM>(a.ncopy, g, off);
+              node_offsets<DIM, D>(m, g, DIM, off);
               float idg[DIM], pv[DIM], rv[DIM], dv[DIM], ev[DIM][1 << DIM];
 #pragma unroll
               for (int c = 0; c < DIM; ++c) {

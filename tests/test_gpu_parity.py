@@ -237,6 +237,27 @@ def test_full_size_runs_are_bit_identical(n):
     for a, b in zip(*runs):
         assert np.array_equal(a, b)
 
+
+@pytest.mark.parametrize("precision,n,p,q1", [("fp32_ir", 16, 4, 6), ("bf16tc_ir", 16, 4, 6), ("fp32_ir", 12, 3, 6),
+                                              ("fp32_ir", 24, 2, 4)])
+def test_precision_forms_are_bit_identical_across_runs(precision, n, p, q1):
+    """The precision forms' solvers (several element batches per CTA at p >= 3, a
+    software-pipelined gather at p = 4) give bit-identical fields and times from run
+    to run."""
+    V = inputs.box_vertices(3, n)
+    runs = []
+    for _ in range(2):
+        ctx = _ctx(3, n, p, q1, V, precision=precision)
+        x, v, e = ctx.init_state()
+        info = ctx.new_step_info(0.0, 1.0)
+        for _ in range(3):
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+        si = ctx.read_step_info(info)
+        assert si.status == 0
+        runs.append((_np(x), _np(v), _np(e), si.cg_iters_total, si.t))
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
 def test_inverted_element_is_reported():
     V = inputs.box_vertices(2, 2)
     ctx = _ctx(2, 2, 1, 2, V)
