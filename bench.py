@@ -46,7 +46,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one launch of the roofline kernel, from one ncu
 # capture of the current kernel (profiles/k_cg_tg3d24_q2_fp64.md); None where
 # no capture of the current kernel exists.
-TRAFFIC = {("tg3d_24_q2", "fp64"): 23420928}
+TRAFFIC = {("tg3d_24_q2", "fp64"): 23637760}
 METRIC = "MDOF/s of PA force+mass path (RK2-average step, H1 vector DOFs per second)"
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
