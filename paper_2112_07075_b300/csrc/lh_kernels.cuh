@@ -722,6 +722,12 @@ struct Family {
   static constexpr int NBC = NB * CGM;          // elements per solver CTA and batch
   static constexpr int TC = THREADS * CGM;      // threads per solver CTA
   static constexpr int CXC = NBC * DIM;
+  // FP64 solver CTAs per SM the register allocation must allow (launch bounds of
+  // k_cg): two, as the solver has been measured with (barriers and memory round
+  // trips bound it as much as FP64 work); 2D Q3 runs one CTA per SM with more
+  // registers, also as measured. Without the bound ptxas may take 98 registers at
+  // Q3/Q4 and halve the occupancy.
+  static constexpr int CG_MINB = DIM == 2 && P == 3 ? 1 : 2;
   static constexpr int MC_S = max3(interp_scratch<DIM, D, Q>(CXC), interp_scratch<DIM, Q, D>(CXC), 0);
 
   // E-vector of M u for one batch: y = B^T diag(mq) B u (CXC tensors), T arithmetic.
@@ -789,14 +795,22 @@ struct Family {
 
   // FP32 sweeps of the precision form use their own, larger element batches
   // (FP32 arithmetic is cheap, so batch latency dominates): as many elements as
-  // fit in ~96 KB of shared memory, at most 64.
+  // fit in ~96 KB of shared memory (~64 KB at 3D Q2), at most 64.
   static constexpr int PER_ELEM_F = 2 * DIM * ND + DIM * NQ +
                                     (interp_scratch<DIM, D, Q>(DIM) > interp_scratch<DIM, Q, D>(DIM)
                                          ? interp_scratch<DIM, D, Q>(DIM) : interp_scratch<DIM, Q, D>(DIM));
 #ifndef LH_NBF_FLOATS
 #define LH_NBF_FLOATS 24000
 #endif
-  static constexpr int NBF_RAW = LH_NBF_FLOATS / PER_ELEM_F;
+#ifndef LH_NBF_FLOATS_3D_Q2
+#define LH_NBF_FLOATS_3D_Q2 16000
+#endif
+  // 3D Q2 takes a smaller budget (32 elements per batch instead of 48): measured
+  // 9 % faster per FP32 step at 24^3 (1.5 batches per CTA, more L1 beside the
+  // smaller shared-memory footprint), 3 % slower at 32^3; every other family keeps
+  // 24,000 floats (both directions measured slower at Q3 and Q4)
+  static constexpr int NBF_BUDGET = DIM == 3 && P == 2 ? LH_NBF_FLOATS_3D_Q2 : LH_NBF_FLOATS;
+  static constexpr int NBF_RAW = NBF_BUDGET / PER_ELEM_F;
   static constexpr int NBF = NBF_RAW < 1 ? 1 : (NBF_RAW > 64 ? 64 : NBF_RAW);
   static constexpr int CXF = NBF * DIM;
   static constexpr int MF_S = max3(interp_scratch<DIM, D, Q>(CXF), interp_scratch<DIM, Q, D>(CXF), 0);
@@ -2162,7 +2176,9 @@ __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_force_t(ForceTAr
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_mass(MassArgs a) { Family<DIM, P, Q>::body_mass(a, blockIdx.x * Family<DIM, P, Q>::NB); }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::TC) k_cg(CgArgs a) { Family<DIM, P, Q>::body_cg(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::TC, Family<DIM, P, Q>::CG_MINB) k_cg(CgArgs a) {
+  Family<DIM, P, Q>::body_cg(a);
+}
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::TC) k_cg_ir(CgIrArgs a) { Family<DIM, P, Q>::body_cg_ir(a); }
 template <int DIM, int P, int Q>
