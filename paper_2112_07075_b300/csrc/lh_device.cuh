@@ -296,6 +296,25 @@ __device__ __forceinline__ double warp_sum_partials(const double *p, int n) {
   return warp_sum(s);
 }
 
+// FP32 twin of warp_sum_partials (same order: lane l adds p[l], p[l + 32], ...,
+// then the lanes are summed by xor shuffles).
+__device__ __forceinline__ float warp_sum_partials_f(const float *p, int n) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.0f;
+  int i = lane;
+  for (; i + 7 * 32 < n; i += 8 * 32) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = p[i + 32 * j];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += v[j];
+  }
+  for (; i < n; i += 32) s += p[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // Device status word: the first error wins.
 // ---------------------------------------------------------------------------

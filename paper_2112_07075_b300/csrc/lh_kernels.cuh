@@ -728,6 +728,9 @@ struct Family {
   // registers, also as measured. Without the bound ptxas may take 98 registers at
   // Q3/Q4 and halve the occupancy.
   static constexpr int CG_MINB = DIM == 2 && P == 3 ? 1 : 2;
+  // the same for the precision form's solver (k_cg_ir), as measured: two CTAs per
+  // SM up to p = 2 and at 3D Q3, one at 2D Q3 and at Q4 (registers)
+  static constexpr int CGIR_MINB = P <= 2 || (DIM == 3 && P == 3) ? 2 : 1;
   static constexpr int MC_S = max3(interp_scratch<DIM, D, Q>(CXC), interp_scratch<DIM, Q, D>(CXC), 0);
 
   // E-vector of M u for one batch: y = B^T diag(mq) B u (CXC tensors), T arithmetic.
@@ -1191,17 +1194,19 @@ struct Family {
         if (status) latch_status(a.status, status);
       }
     };
-    // FP32 block sums of 5 values into thread 0's v (warp shuffles).
-    auto block_sum_f = [&](float (&v)[5]) {
+    // FP32 block sums of the N <= 5 values of v into thread 0's v (warp shuffles).
+    auto block_sum_f = [&](auto &v) {
+      constexpr int N = (int)(sizeof(v) / sizeof(v[0]));
+      static_assert(N <= 5, "reduction scratch holds five values");
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-      for (int k = 0; k < 5; ++k)
+      for (int k = 0; k < N; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
       __syncthreads();
       if (lane == 0)
-        for (int k = 0; k < 5; ++k) redf[k * 32 + warp] = v[k];
+        for (int k = 0; k < N; ++k) redf[k * 32 + warp] = v[k];
       __syncthreads();
       if (warp == 0)
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < N; ++k) {
           float t = lane < nw ? redf[k * 32 + lane] : 0.0f;
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
           v[k] = t;
@@ -1222,7 +1227,7 @@ struct Family {
       // ---- O-B: FP64 residual and its FP32 copy; inner start d = 0
       {
         double acc[2] = {0.0, 0.0};   // b.b, r.r
-        float accf[5] = {0, 0, 0, 0, 0};   // r32.r32, r32.z32
+        float accf[2] = {0, 0};   // r32.r32, r32.z32
         for (int g = gtid; g < nh1; g += gstride) {
           int off[1 << DIM];
           const int n = node_copies<DIM, D>(m, g, DIM, off);
@@ -1265,12 +1270,7 @@ struct Family {
         const double s0 = outer == 0 ? warp_sum_partials(a.partials, G) : 0.0;
         const double s1 = warp_sum_partials(a.partials + G, G);
         float f[2];
-        for (int k2 = 0; k2 < 2; ++k2) {
-          float t = 0.0f;
-          for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)k2 * G + i];
-          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          f[k2] = t;
-        }
+        for (int k2 = 0; k2 < 2; ++k2) f[k2] = warp_sum_partials_f(pf + (size_t)k2 * G, G);
         if (threadIdx.x == 0) { s_sc[0] = s0; s_sc[1] = s1; s_f[0] = f[0]; s_f[1] = f[1]; }
       }
       __syncthreads();
@@ -1304,15 +1304,13 @@ struct Family {
         {
           float pq = 0.0f;
           const bool swept = inner_sweep(beta, pq);
-          float acc[5] = {pq, 0, 0, 0, 0};
+          float acc[1] = {pq};
           block_sum_f(acc);
           if (threadIdx.x == 0) pf[(size_t)2 * G + blockIdx.x] = acc[0];
           if (!swept || !sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
         }
         if (threadIdx.x < 32) {
-          float t = 0.0f;
-          for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)2 * G + i];
-          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          const float t = warp_sum_partials_f(pf + (size_t)2 * G, G);
           if (threadIdx.x == 0) s_f[2] = rz / t;
         }
         __syncthreads();
@@ -1320,7 +1318,7 @@ struct Family {
         {  // one node sweep: q = M p_new gathered, p = p_new, d += alpha p, r -= alpha q,
            // r.r and r.z; one (node, component) per work item, copies through the
            // node-copy table, every load issued first
-          float acc[5] = {0, 0, 0, 0, 0};
+          float acc[2] = {0, 0};
           if constexpr (P >= 3) {
             // high orders: one node per work item, the loads of all DIM components in
             // flight together (FP32 leaves the registers)
@@ -1396,15 +1394,10 @@ struct Family {
           }
         }
         if (!sync()) { finish(inner_total + it, kStatusTimeout, rr64, bb); return; }
-        if (threadIdx.x < 32) {
-          float v[2];
-          for (int k2 = 0; k2 < 2; ++k2) {
-            float t = 0.0f;
-            for (int i = threadIdx.x; i < G; i += 32) t += pf[(size_t)k2 * G + i];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            v[k2] = t;
-          }
-          if (threadIdx.x == 0) { s_f[0] = v[0]; s_f[1] = v[1]; }
+        if (threadIdx.x < 64) {   // r.r on warp 0, r.z on warp 1, side by side
+          const int w = threadIdx.x >> 5;
+          const float t = warp_sum_partials_f(pf + (size_t)w * G, G);
+          if ((threadIdx.x & 31) == 0) s_f[w] = t;
         }
         __syncthreads();
         rr = s_f[0];
@@ -2180,7 +2173,9 @@ __global__ void __launch_bounds__(Family<DIM, P, Q>::TC, Family<DIM, P, Q>::CG_M
   Family<DIM, P, Q>::body_cg(a);
 }
 template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(Family<DIM, P, Q>::TC) k_cg_ir(CgIrArgs a) { Family<DIM, P, Q>::body_cg_ir(a); }
+__global__ void __launch_bounds__(Family<DIM, P, Q>::TC, Family<DIM, P, Q>::CGIR_MINB) k_cg_ir(CgIrArgs a) {
+  Family<DIM, P, Q>::body_cg_ir(a);
+}
 template <int DIM, int P, int Q>
 __global__ void __launch_bounds__(Family<DIM, P, Q>::THREADS) k_geom(GeomArgs a) { Family<DIM, P, Q>::body_geom(a); }
 template <int DIM, int P, int Q>
