@@ -296,6 +296,15 @@ __device__ __forceinline__ double warp_sum_partials(const double *p, int n) {
   return warp_sum(s);
 }
 
+// This block's work items [k0, k1) when n items are split into gridDim.x
+// contiguous chunks of equal size (+-1): every block, hence every SM, gets the
+// same share (a grid-stride loop gives the first blocks one item more per thread).
+__device__ __forceinline__ void block_chunk(int n, int &k0, int &k1) {
+  const int G = gridDim.x, b = blockIdx.x, base = n / G, rem = n % G;
+  k0 = b * base + (b < rem ? b : rem);
+  k1 = k0 + base + (b < rem ? 1 : 0);
+}
+
 // FP32 twin of warp_sum_partials (same order: lane l adds p[l], p[l + 32], ...,
 // then the lanes are summed by xor shuffles).
 __device__ __forceinline__ float warp_sum_partials_f(const float *p, int n) {

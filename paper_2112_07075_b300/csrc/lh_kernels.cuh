@@ -1077,7 +1077,13 @@ struct Family {
          // z = invdiag r, r.r and r.z; one (node, component) per work item, its
          // copies located through the node-copy table, every load issued first
         double acc[2] = {0.0, 0.0};
-        for (int k = gtid; k < DIM * nh1; k += gstride) {
+        // one contiguous share of equal size per block: the sweep is FP64-issue
+        // bound per SM, and a grid-stride split gives the first blocks (2 of 3 SMs
+        // at 24^3 Q2) one item more per thread (measured 1.35 % per step; the
+        // latency-bound FP32 node sweeps keep the grid-stride split, measured faster)
+        int k0, k1;
+        block_chunk(DIM * nh1, k0, k1);
+        for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
           const int c = DIM == 2 ? (k >= nh1 ? 1 : 0) : (k >= 2 * nh1 ? 2 : (k >= nh1 ? 1 : 0));
           const int g = k - c * nh1;
           int off[1 << DIM];
