@@ -1097,7 +1097,10 @@ struct Family {
 #pragma unroll
           for (int j = 1; j < (1 << DIM); ++j)
             if (off[j] >= 0) qv += ev[j];
-          if (idg != 0.0) {   // constrained DOFs keep p = r = z = 0
+          // constrained DOFs (Jacobi inverse exactly +0) keep p = r = z = 0; the test
+          // reads the bit pattern, so it runs on the integer pipe and leaves the FP64
+          // pipe, which bounds this sweep, to the arithmetic
+          if (__double_as_longlong(idg) != 0LL) {
             const double pn = fma(beta, pv, zv);
             const double r2 = fma(-alpha, qv, rv);
             const double z2 = r2 * idg;
