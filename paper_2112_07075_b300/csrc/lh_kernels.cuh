@@ -852,7 +852,7 @@ struct Family {
         __syncthreads();
         gather_regs(nb);
         // every warp has read eb before the loop overwrites it with the next batch's
-        // base nodes (the loads it issued stay in flight across the barrier)
+        // base nodes (one barrier per sweep; no measurable cost at 32^3 Q4)
         __syncthreads();
       }
       for (; bt < nbatch; bt += gridDim.x) {
