@@ -216,7 +216,7 @@ lh_status lh_mass_mult_tc(lh_ctx *ctx, const float *x, float *y, lh_stream_t str
  * guess, out = solution. b, x: DEVICE [dim][N_H1]. info: DEVICE lh_cg_info or NULL.
  * With the context's precision LH_PRECISION_FP64, max_it bounds the CG iterations;
  * with LH_PRECISION_FP32_IR (LH_PRECISION_BF16TC_IR) each refinement step runs an
- * FP32 PCG to a relative residual of 1e-5 (1e-4) (at most 200 iterations), at most
+ * FP32 PCG to a relative residual of 1e-6 (3e-5) (at most 200 iterations), at most
  * 40 steps are taken, max_it bounds the total inner iterations, and info->iters
  * reports that total.
  * One persistent cooperative launch; convergence is decided on the device. */
