@@ -24,7 +24,7 @@ Sources followed (arXiv 2112.07075):
 
 Where the paper is silent (force-matrix entries, equation of state, artificial
 viscosity, time integrator, time-step estimate, bases, quadrature, boundary
-conditions) the oracle follows the readings listed in the design doc, restated in
+conditions) the oracle follows one stated reading per gap, written out in
 each module's docstrings.
 
 Parity status per function is stated in each module header. Functions whose

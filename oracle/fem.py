@@ -7,7 +7,7 @@ the 1D tables (Section 3.2, phi_i(q_k) = phi^1d_{i1}(q_k1) phi^1d_{i2}(q_k2)),
 so the oracle never uses sum factorization: every operator is a dense element
 matrix assembled into a global scipy.sparse matrix (Table 1, first row).
 
-Definitions (readings of Sections 2.1 and 3.3, see DESIGN.md):
+Definitions (readings of Sections 2.1 and 3.3):
   Jacobian      J[c,l](q) = sum_i x_{c,i} dw_i/dxi_l(q)
   mass          M_ij = sum_e sum_q omega_q rho0 detJ0 w_i w_j, M_v = I_d (x) M
                 (the element matrix of Section 3.2 with |J| weighted by rho0)

@@ -7,7 +7,7 @@ The paper (Section 2.1) says only that the total stress is the physical stress
 plus a stress due to artificial viscosity, and (Section 6) that quadrature-point
 data, artificial-viscosity coefficients and the time step are computed per
 quadrature point; it refers the formulas to its citations. The readings below
-(single material, ideal gas, tensor viscosity) are stated in the design doc:
+(single material, ideal gas, tensor viscosity) are:
 
   density     rho = rho0 detJ0 / detJ                         (Eq. 16, rho|J| = rho0|J0|)
   EOS         e+ = max(e, 0), p = (gamma-1) rho e+, cs = sqrt(gamma (gamma-1) e+)
@@ -35,9 +35,17 @@ Pins (tests/test_oracle_qpoint.py): eigenvalues and eigenvector residuals vs
 numpy.linalg.eigh on random and degenerate matrices; an affine velocity v = A x
 gives eps = sym(A) exactly; an undeformed Cartesian mesh at t = 0 gives J = h I,
 hmin = h / p and the closed-form dt; rho detJ = rho0 detJ0.
-The choice of eigenvector among an eigenspace of dimension > 1, the constants
-1e-12 / 2.5 / 0.5 and the exact form of the AV coefficient are fixed by the
-reading only: parity unpinned by the paper for those parts.
+Viscosity pins (tests/test_oracle_viscosity.py), each value worked out by hand
+from an affine construction: uniform compression v = -alpha x (mu = 2 h0^2 alpha
++ h0 c_s / 2, D, dt); a stretched mesh with v_1 = -alpha x_1 (h = 2 h0, rho < 1);
+a sheared initial mesh moved by a non-commuting affine map with a strain rate of
+chosen eigenpairs of mixed sign (h = h0 |J J0^{-1} s|, mu, rho, D, dt) and of pure
+expansion (linear term off). Each of eight planted mistakes (coefficients 1 for
+2 and for 1/2, J0^{-1} J, the largest eigenvalue in 2D and 3D, a dropped absolute
+value, the linear-term switch on -lam, an undeformed length scale) fails a pin.
+Still fixed by the reading only (parity unpinned by the paper): the choice of
+eigenvector inside an eigenspace of dimension > 1 and the constants 1e-12 / 2.5
+themselves (the pins fix the formula as read, not that the paper means it).
 """
 from __future__ import annotations
 

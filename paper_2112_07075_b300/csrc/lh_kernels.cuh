@@ -189,7 +189,7 @@ __device__ __forceinline__ T gather_node(const MeshDesc &m, const T *evec, int C
 }
 
 // ---------------------------------------------------------------------------
-// Per-qpoint physics (reading of Sections 2.1 and 6, see DESIGN.md):
+// Per-qpoint physics (reading of Sections 2.1 and 6):
 // EOS, tensor artificial viscosity, stress, force data and time-step bound.
 // ---------------------------------------------------------------------------
 constexpr double kEps0 = 1.0e-12;
