@@ -297,6 +297,8 @@ def run_ours(args):
         "force_mult_t": {"ms": t_ft, "tflops": W["force_t_flops"] / (t_ft * 1e-3) / 1e12},
         "force_pair": {"rate_mdofs": sz.nv / ((t_f + t_ft) * 1e-3) / 1e6},
     }
+    whole = whole_run(ctx, wl, flush, stream) if (not trajectory and world == 1) else None
+
     # Roofline of the dominant kernel, measured live over the timed steps: the
     # library's event pairs around each solver launch (same stream) give its
     # time; algorithmic FLOPs = iterations x CG-iteration FLOPs + one matvec per solve.
@@ -393,6 +395,7 @@ def run_ours(args):
             "gpu_launches": 13 * K,
             "clocks": clocks,
             "kernels": kernels,
+            "whole_run": whole,
             "forms": {"precision": forms, "batching": batching, "learned": learned},
             "remap": remap,
             "stiffness": stiffness,
@@ -403,6 +406,8 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, V)
+            if REDUCED_STATES:
+                line["forms_vs_oracle"] = forms_vs_oracle()
             if remap is not None:
                 remap["cpu_baseline"] = remap_cpu_baseline()
             if stiffness is not None:
@@ -468,6 +473,115 @@ def measure_form(wl_name, precision, steps, warmup, flush, seed=3):
     return out, state
 
 
+def whole_run(ctx, wl, flush, stream):
+    """The configured run from t = 0 to t_end (CFL steps), every step timed with CUDA
+    events after an L2 flush: the whole-run rate beside the timed window's."""
+    import torch
+    x, v, e = ctx.init_state("taylor_green")
+    info = ctx.new_step_info(0.0, wl["t_end"])
+    ev = []
+    k = 0
+    it0 = ctx.read_step_info(info).cg_iters_total
+    while True:
+        for _ in range(16):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(float(k))
+            a.record(stream)
+            ctx.rk2avg_step(x, v, e, 0.0, info)
+            b.record(stream)
+            ev.append((a, b))
+            k += 1
+        si = ctx.read_step_info(info)
+        if wl["t_end"] - si.t <= 1e-12 * wl["t_end"] or k > 100000:
+            break
+        if si.dt > 0 and wl["t_end"] - si.t <= 20.0 * si.dt:
+            while wl["t_end"] - ctx.read_step_info(info).t > 1e-12 * wl["t_end"]:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(float(k))
+                a.record(stream)
+                ctx.rk2avg_step(x, v, e, 0.0, info)
+                b.record(stream)
+                ev.append((a, b))
+                k += 1
+            break
+    torch.cuda.synchronize()
+    si = ctx.read_step_info(info)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    tot = sum(ms) / 1e3
+    return {"value": ctx.sizes.nv * k / tot / 1e6, "unit": "MDOF/s", "steps": k,
+            "ms_per_step": 1e3 * tot / k, "t_final": si.t, "status": ctx.sync_status(),
+            "cg_iters_per_solve": (si.cg_iters_total - it0) / (2.0 * k),
+            "window": f"whole run from t = 0 to t = {wl['t_end']}, every step timed (L2 flushed)"}
+
+
+# Reduced cases of the precision and learned workloads, small enough for the oracle:
+# the same element families, jitter and seeds as the full-size configurations, on 6^3
+# meshes, with CFL 0.5 steps from t = 0 (10 steps for the precision workload, 20 for
+# the learned one). The GPU legs store their end states here; the CPU-baseline leg
+# runs the oracle on the same cases and reports each form's error against it.
+REDUCED = {
+    "tg3d_6_q4_jit": dict(dim=3, n=6, order=4, q1=6, jitter=0.15, seed=3, steps=10,
+                          desc="3D Taylor-Green 6^3 Q4/Q3 q6, jitter 0.15h (seed 3), 10 CFL steps"),
+    "tg3d_6_q3_jit": dict(dim=3, n=6, order=3, q1=6, jitter=0.1, seed=9, steps=20,
+                          desc="3D Taylor-Green 6^3 Q3/Q2 q6, jitter 0.1h (held-out seed 9), 20 CFL steps"),
+}
+REDUCED_STATES = {}   # (case, mode) -> (x, v, e) end state of the GPU run
+
+
+def reduced_run(case, precision, net=None):
+    """End state of a reduced case after its CFL steps, one form (net: learned guess)."""
+    from paper_2112_07075_b300 import inputs
+    from paper_2112_07075_b300.lh import Context, learn_attach
+    rc = REDUCED[case]
+    V = inputs.box_vertices(rc["dim"], rc["n"], jitter=rc["jitter"], seed=rc["seed"])
+    c = Context(rc["dim"], rc["n"], V, rc["order"], rc["q1"], precision=precision)
+    if net is not None:
+        learn_attach(c, net, 2)
+    x, v, e = c.init_state("taylor_green")
+    info = c.new_step_info(0.0, 1.0)
+    for _ in range(rc["steps"]):
+        c.rk2avg_step(x, v, e, 0.0, info)
+    si = c.read_step_info(info)
+    out = tuple(t.cpu().numpy() for t in (x, v, e))
+    st = c.sync_status()
+    c.close()
+    if st != 0 or si.steps != rc["steps"]:
+        raise RuntimeError(f"reduced run {case}/{precision}: status {st}, {si.steps} steps")
+    mode = precision + ("+learned" if net is not None else "")
+    REDUCED_STATES[(case, mode)] = out
+    return out
+
+
+def forms_vs_oracle():
+    """CPU-baseline leg: the oracle on every reduced case that has GPU end states, and the
+    relative per-field error (x, v, e) of each form's end state against it."""
+    from paper_2112_07075_b300 import inputs
+    from oracle.hydro import Hydro, Params
+    rep = {}
+    for case in sorted({k[0] for k in REDUCED_STATES}):
+        rc = REDUCED[case]
+        V = inputs.box_vertices(rc["dim"], rc["n"], jitter=rc["jitter"], seed=rc["seed"])
+        hy = Hydro(Params(dim=rc["dim"], n=rc["n"], order=rc["order"], q1=rc["q1"], vertices=V))
+        x, v, e = hy.initial_state("taylor_green")
+        t0 = time.perf_counter()
+        t = 0.0
+        for _ in range(rc["steps"]):
+            x, v, e, oi = hy.rk2avg_step(x, v, e, dt=None, t=t, t_end=1.0)
+            t += oi.dt
+        el = time.perf_counter() - t0
+        ref = (x, v, e.reshape(-1))
+        errs = {}
+        for (c2, mode), st in REDUCED_STATES.items():
+            if c2 != case:
+                continue
+            errs[mode] = {f: float(np.linalg.norm(a.reshape(-1) - b) / np.linalg.norm(b))
+                          for f, a, b in zip(("x", "v", "e"), st, (r.reshape(-1) for r in ref))}
+            errs[mode]["max"] = max(errs[mode].values())
+        rep[case] = {"workload": rc["desc"], "oracle_s": el, "cores": _cores(),
+                     "rel_field_err_vs_oracle": errs, "bar": 1e-10}
+    return rep
+
+
 def forms_report(flush, steps=3, warmup=1):
     rep = {}
     for wl_name in ("tg3d_24_q2", "tg3d_32_q4_jit"):
@@ -483,6 +597,9 @@ def forms_report(flush, steps=3, warmup=1):
             rep[wl_name]["bf16tc_ir"]["speedup_vs_fp64"] = f64["ms_per_step"] / ftc["ms_per_step"]
             rep[wl_name]["bf16tc_ir"]["max_rel_field_diff_vs_fp64_gpu"] = max(
                 float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(stc, s64))
+    for prec in ("fp64", "fp32_ir", "bf16tc_ir"):
+        reduced_run("tg3d_6_q4_jit", prec)
+    rep["vs_oracle"] = "reduced case tg3d_6_q4_jit, filled in by the CPU-baseline leg (cpu_checks)"
     return rep
 
 
@@ -524,31 +641,70 @@ def batching_report(flush, steps=5, warmup=2, seed=4):
     b.record(stream)
     b.synchronize()
     single_ms = a.elapsed_time(b) / steps
-    # batched: one graph launch per step
+    # batched: one graph launch per step, first with the default tiles (all 1, 256
+    # threads), then with the autotuned ones; both from the same initial states
     batch = Batch(ctxs, states, dts)
-    tiles = batch.autotune()
-    for _ in range(warmup):
-        batch.step()
-    ts = []
-    for _ in range(steps):
-        flush.fill_(6.0)
-        a, b = ev(), ev()
-        a.record(stream)
-        batch.step()
-        b.record(stream)
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
+    init = [tuple(t.clone() for t in st) for st in states]
+    info0 = batch.infos.clone()
+
+    def run_batched():
+        for st, st0 in zip(states, init):
+            for t, t0 in zip(st, st0):
+                t.copy_(t0)
+        batch.infos.copy_(info0)
+        for _ in range(warmup):
+            batch.step()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(6.0)
+            a, b = ev(), ev()
+            a.record(stream)
+            batch.step()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    batch.set_config()
+    default_ms = run_batched()
+    for st, st0 in zip(states, init):
+        for t, t0 in zip(st, st0):
+            t.copy_(t0)
+    batch.infos.copy_(info0)
+    t_tune = time.perf_counter()
+    cfg = batch.autotune()
+    tune_s = time.perf_counter() - t_tune
+    batched_ms = run_batched()
     infos_b = batch.read_infos()
-    batched_ms = statistics.mean(ts)
     st = max(i.status for i in infos_b)
+    # algorithmic FP64 FLOPs of the timed steps: per problem and stage the qdata
+    # contractions, F.1, F^T v and (iterations + 1) mass actions with the CG vector work
+    flops = 0.0
+    for c, inf in zip(ctxs, infos_b):
+        W = work_model(2, c.order, c.q1, c.sizes.ne, c.sizes.n_h1)
+        D_, Q_, L_ = c.order + 1, c.q1, c.order
+        grad = 2 * Q_ * D_ * D_ + 2 * Q_ * Q_ * D_
+        l2i = Q_ * L_ * L_ + Q_ * Q_ * L_
+        qd = 2 * c.sizes.ne * (2 * 2 * grad + l2i)
+        it = sum(inf.cg_iters)   # iterations of the last step's two solves
+        flops += 2 * (qd + W["force_flops"] + W["force_t_flops"] + W["mass_flops"]) + it * W["cg_iter_flops"]
+    peak64, _ = probe_peaks()
+    achieved = flops / (batched_ms * 1e-3) / 1e12
     rep = {"problems": len(probs), "total_nv": nv, "orders": {p: sum(q["order"] == p for q in probs) for p in range(1, 5)},
-           "setup_s": setup_s, "tiles_per_order": tiles,
+           "setup_s": setup_s, "tile_config": cfg, "autotune_s": tune_s,
+           "default_config_ms_per_step": default_ms, "autotune_gain": default_ms / batched_ms,
            "batched_ms_per_step": batched_ms, "batched_mdofs": nv / (batched_ms * 1e-3) / 1e6,
            "one_by_one_ms_per_step": single_ms, "one_by_one_mdofs": nv / (single_ms * 1e-3) / 1e6,
            "speedup": single_ms / batched_ms, "status": st,
            "cg_iters_max": max(max(i.cg_iters) for i in infos_b),
-           "launches_per_step": 16, "note": "one CUDA-graph launch per batched step: 10 kernels + 2 cooperative "
-                                            "solver launches + 4 memsets"}
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                        "frac": achieved / peak64, "flops_per_step": flops,
+                        "note": "algorithmic FP64 FLOPs of the whole batched step (contractions and CG vector "
+                                "work, last step's iteration counts) over its CUDA-event time; peak = the FP64 "
+                                "FMA-chain probe"},
+           "launches_per_step": 6, "note": "one CUDA-graph launch per batched step: per stage the fused "
+                                           "qdata + F.1 element pass, one cooperative solver launch (rhs gather, "
+                                           "solves, node update) and the F^T v element pass"}
     batch.close()
     for c in ctxs:
         c.close()
@@ -638,6 +794,9 @@ def learned_report(flush, eval_n=48, eval_steps=6, train_n=16, train_seeds=8, tr
             out[mode]["learned_guess_used"] = used
             out[mode]["predictions"] = preds
             out[mode]["mean_initial_residual_ratio_learned_vs_previous"] = statistics.mean(ratios)
+    for prec, use_net in (("fp64", False), ("fp32_ir", False), ("fp32_ir", True), ("bf16tc_ir", True)):
+        reduced_run("tg3d_6_q3_jit", prec, net if use_net else None)
+    out["vs_oracle"] = "reduced case tg3d_6_q3_jit, filled in by the CPU-baseline leg (cpu_checks)"
     base = finals["fp64"]
     for mode in modes[1:]:
         out[mode]["max_rel_field_diff_vs_fp64_gpu"] = max(

@@ -423,14 +423,32 @@ typedef struct lh_batch lh_batch;
 lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *const *v, double *const *e,
                           const double *dt, lh_step_info *infos, lh_batch **out);
 
-/* Choose, per order, how many element batches one work item holds (1, 2 or 4)
- * by timing the batched element kernels (which leave the state unchanged).
- * tiles_out: optional HOST int[4], the chosen tiles for orders 1..4. Synchronous. */
-lh_status lh_batch_autotune(lh_batch *b, int *tiles_out);
+/* Tile shapes of the batched step (the RAJA-teams style tiles of Section 4.2, as
+ * an autotuned choice): cfg[0..3] = element batches per work item of the element
+ * passes for orders 1..4 (1, 2 or 4), cfg[4..7] = element batches per work item
+ * of the solver for orders 1..4 (1, 2 or 4), cfg[8] = threads per block of the
+ * element passes, i.e. how many threads share one tile's quadrature slab (128,
+ * 256 or 512; every per-value result is the same for any choice).
+ *
+ * lh_batch_autotune times whole batched steps (element passes and solver) for
+ * candidate shapes -- per order element tiles 1, 2, 4 and solver tiles 1, 2, then
+ * 128, 256, 512 threads per block -- and keeps each change that makes the step at
+ * least 1 % faster. Every trial starts from the same state and the problems'
+ * states, warm starts and step records are restored at the end, so tuning leaves
+ * no trace in the results. cfg_out: optional HOST int[9], the chosen shape.
+ * Synchronous; allocates and frees one snapshot buffer of the problems' states.
+ * lh_batch_set_config sets a shape directly (HOST int[9]; LH_ERR_ARG for values
+ * outside the lists above). The default is all tiles 1 and 256 threads. */
+lh_status lh_batch_autotune(lh_batch *b, int *cfg_out);
+lh_status lh_batch_set_config(lh_batch *b, const int *cfg);
 
 /* One RK2-average step of every problem (fixed dt per problem), enqueued on
  * `stream` as one CUDA graph launch (captured on the first call and whenever
- * rel_tol or max_it change; rel_tol <= 0: 1e-12, max_it <= 0: 1000). */
+ * rel_tol, max_it or the tile shape change; rel_tol <= 0: 1e-12, max_it <= 0:
+ * 1000). The graph holds six launches, three per stage: the fused quadrature-data
+ * and F.1 element pass; one cooperative launch with the right-hand-side gather,
+ * every problem's mass solve and the stage's node update; the F^T v element pass
+ * with the energy update. */
 lh_status lh_batch_step(lh_batch *b, double rel_tol, int max_it, lh_stream_t stream);
 
 /* Message of the last error of a batch call. */
@@ -511,16 +529,23 @@ lh_status lh_learn_stats(const lh_ctx *ctx, int *rows_recorded, int *solves, int
  * x, y: DEVICE [dim][N_H1], must not alias; y is overwritten, no boundary
  *   conditions are applied.
  * Scratch: the element vector (dim * NE * (order+1)^dim doubles) lives in a
- *   file-scope static device array of 32 MiB (plus a 4 KiB basis-table array);
- *   every GPU that loads liblh holds these until the process exits. Larger meshes
- *   are rejected with LH_ERR_ARG and a message giving the bytes needed, before
- *   anything is enqueued. The scratch holds the previous call's contents; every
- *   entry this call reads is written first by this call, so nothing has to start
- *   at zero.
- * Set-up: the first call on each device (with that device current) looks up the
- *   arrays' device addresses with cudaGetSymbolAddress; make that first call
- *   before any stream capture. The basis table is uploaded on `stream` with a
- *   cudaMemcpyAsync from host memory at every call.
+ *   file-scope static device array of 32 MiB (plus a 24 KiB array with the basis
+ *   tables of every compiled family); every GPU that loads liblh holds these until
+ *   the process exits. Larger meshes are rejected with LH_ERR_ARG and a message
+ *   giving the bytes needed, before anything is enqueued. The scratch holds the
+ *   previous call's contents; every entry this call reads is written first by
+ *   this call, so nothing has to start at zero.
+ * Set-up: the first call on each device (with that device current) does a
+ *   one-time set-up: it looks up the arrays' device addresses with
+ *   cudaGetSymbolAddress, uploads the basis tables of every compiled family with
+ *   a synchronous cudaMemcpy followed by cudaDeviceSynchronize, and sets the mass
+ *   kernels' shared-memory attribute. Make that first call before any stream
+ *   capture. With CUDA's default lazy module loading, the first use of the
+ *   library's kernels on a device also loads its module, and the two static
+ *   arrays are created on the device at that moment: an application that hands
+ *   all device memory to its own pool should make the first call at start-up,
+ *   before the pool takes the memory (or run with CUDA_MODULE_LOADING=EAGER).
+ *   Every later call only enqueues two kernels on `stream`.
  * Concurrency: all calls share the one scratch array per device, so calls whose
  *   execution overlaps on the GPU (different streams without ordering, or
  *   several host threads) race and give wrong results; order them on one stream.

@@ -1,12 +1,17 @@
 // Batching form: many independent 2D problems of uneven order (p = 1..4,
-// q1 = 2p) and mesh size advanced together. Every hot-path operation of an
-// RK2-average step is ONE persistent launch over all problems: element work
-// items (problem, first element, batch count) sorted by order dispatch to the
-// compiled kernel family of their order; node work items cover node ranges. The
-// mass solves of all problems run in one cooperative launch with per-problem
-// scalars and convergence. The whole step is captured once into a CUDA graph
-// and replayed. Per-order tiles (element batches per work item) are chosen by a
-// timing autotuner. Each problem keeps its own lh_ctx for set-up and buffers.
+// q1 = 2p) and mesh size advanced together. Each stage of an RK2-average step
+// is three persistent launches over all problems: (1) the element pass of the
+// quadrature data fused with F.1 (both element-local), (2) one cooperative
+// launch that gathers the right-hand side, runs every problem's mass solve with
+// its own scalars and convergence test, and applies the stage's node update,
+// (3) the element pass of F^T v with the energy update. Work items (problem,
+// first element, batch count) are sorted by order and dispatch to the compiled
+// kernel family of their order. The whole step (six launches) is captured once
+// into a CUDA graph and replayed. The tile shapes -- element batches per work
+// item for the element passes and for the solver, per order, and the threads
+// per block of the element passes (threads sharing one element's quadrature
+// slab) -- are picked by an autotuner that times whole steps. Each problem
+// keeps its own lh_ctx for set-up and buffers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,33 +71,28 @@ __device__ __forceinline__ void dispatch_order(int order, F &&f) {
 }
 
 // ---- batched element kernels (one launch for all problems) ----------------
-__global__ void __launch_bounds__(kThreads) k_b_qdata(const QdataArgs *args, const ItemE *items, int nitems) {
+// The element bodies stride every loop by blockDim.x, so any block size gives
+// the same per-value arithmetic: TPB only sets how many threads share the
+// quadrature points of a tile (the autotuner's second axis).
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_b_qf(const QdataArgs *qa, const ForceArgs *fa, const ItemE *items,
+                                              int nitems) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const ItemE w = items[it];
     dispatch_order(w.order, [&](auto P) {
       using F = F2<decltype(P)::value>;
       for (int b = 0; b < w.nbat; ++b) {
-        F::body_qdata(args[w.pid], w.e0 + b * F::NB);
+        F::body_qdata(qa[w.pid], w.e0 + b * F::NB);   // D of these elements ...
+        __syncthreads();
+        F::body_force(fa[w.pid], w.e0 + b * F::NB);   // ... is all F.1 of them needs
         __syncthreads();
       }
     });
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_b_force(const ForceArgs *args, const ItemE *items, int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const ItemE w = items[it];
-    dispatch_order(w.order, [&](auto P) {
-      using F = F2<decltype(P)::value>;
-      for (int b = 0; b < w.nbat; ++b) {
-        F::body_force(args[w.pid], w.e0 + b * F::NB);
-        __syncthreads();
-      }
-    });
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_b_force_t(const ForceTArgs *args, const ItemE *items, int nitems) {
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_b_force_t(const ForceTArgs *args, const ItemE *items, int nitems) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const ItemE w = items[it];
     dispatch_order(w.order, [&](auto P) {
@@ -113,70 +113,56 @@ __device__ __forceinline__ int table_copies(const int *__restrict__ tab, int g, 
   return (t.x >= 0) + (t.y >= 0) + (t.z >= 0) + (t.w >= 0);
 }
 
-// ---- batched node kernels --------------------------------------------------
+// ---- node phases of the batched solver launch (one thread per scalar node) --
 // rhs = -(F.1) gathered from the E-vector, zero on constrained DOFs.
-__global__ void k_b_rhs(const BProb *probs, const ItemN *items, int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const ItemN w = items[it];
-    const BProb &pb = probs[w.pid];
-    const int g = w.g0 + threadIdx.x;
-    if (g < w.g1) {
-      dispatch_order(pb.order, [&](auto P) {
-        constexpr int D = decltype(P)::value + 1, ND = D * D;
-        int off[4];
-        const int n = table_copies(pb.ncopy, g, off);
-        for (int c = 0; c < 2; ++c) {
-          const int k = c * pb.m.nh1 + g;
-          double s = pb.evec[off[0] + c * ND];
-          for (int j = 1; j < n; ++j) s += pb.evec[off[j] + c * ND];
-          pb.rhs[k] = pb.invdiag[k] != 0.0 ? -s : 0.0;
-        }
-      });
+__device__ __forceinline__ void node_rhs(const BProb &pb, const ItemN &w) {
+  const int g = w.g0 + threadIdx.x;
+  if (g >= w.g1) return;
+  dispatch_order(pb.order, [&](auto P) {
+    constexpr int D = decltype(P)::value + 1, ND = D * D;
+    int off[4];
+    const int n = table_copies(pb.ncopy, g, off);
+    for (int c = 0; c < 2; ++c) {
+      const int k = c * pb.m.nh1 + g;
+      double s = pb.evec[off[0] + c * ND];
+      for (int j = 1; j < n; ++j) s += pb.evec[off[j] + c * ND];
+      pb.rhs[k] = pb.invdiag[k] != 0.0 ? -s : 0.0;
     }
-  }
+  });
 }
 
 // Stage-1 update: vb0 = v + dt/2 a0, v_h = vb0, x_h = x + dt/2 vb0.
-__global__ void k_b_mid(const BProb *probs, const ItemN *items, int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const ItemN w = items[it];
-    const BProb &pb = probs[w.pid];
-    const int g = w.g0 + threadIdx.x;
-    if (g < w.g1) {
-      const double hdt = 0.5 * *pb.dt;
-      for (int c = 0; c < 2; ++c) {
-        const int k = c * pb.m.nh1 + g;
-        const double vb = fma(hdt, pb.a[k], pb.v[k]);
-        pb.vh[k] = vb;
-        pb.xh[k] = fma(hdt, vb, pb.x[k]);
-      }
-    }
+__device__ __forceinline__ void node_mid(const BProb &pb, const ItemN &w) {
+  const int g = w.g0 + threadIdx.x;
+  if (g >= w.g1) return;
+  const double hdt = 0.5 * *pb.dt;
+  for (int c = 0; c < 2; ++c) {
+    const int k = c * pb.m.nh1 + g;
+    const double vb = fma(hdt, pb.a[k], pb.v[k]);
+    pb.vh[k] = vb;
+    pb.xh[k] = fma(hdt, vb, pb.x[k]);
   }
 }
 
 // Final update: vb = v + dt/2 a, x += dt vb, v += dt a; node item 0 of a problem
 // also advances its step record.
-__global__ void k_b_final(const BProb *probs, const ItemN *items, int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const ItemN w = items[it];
-    const BProb &pb = probs[w.pid];
-    const int g = w.g0 + threadIdx.x;
-    const double dt = *pb.dt, hdt = 0.5 * dt;
-    if (g < w.g1) {
-      for (int c = 0; c < 2; ++c) {
-        const int k = c * pb.m.nh1 + g;
-        const double ak = pb.a[k], vk = pb.v[k];
-        const double vb = fma(hdt, ak, vk);
-        pb.vb[k] = vb;
-        pb.x[k] = fma(dt, vb, pb.x[k]);
-        pb.v[k] = fma(dt, ak, vk);
-      }
+__device__ __forceinline__ void node_final(const BProb &pb, const ItemN &w) {
+  const int g = w.g0 + threadIdx.x;
+  const double dt = *pb.dt, hdt = 0.5 * dt;
+  if (g < w.g1) {
+    for (int c = 0; c < 2; ++c) {
+      const int k = c * pb.m.nh1 + g;
+      const double ak = pb.a[k], vk = pb.v[k];
+      const double vb = fma(hdt, ak, vk);
+      pb.vb[k] = vb;
+      pb.x[k] = fma(dt, vb, pb.x[k]);
+      pb.v[k] = fma(dt, ak, vk);
     }
-    if (w.k == 0 && threadIdx.x == 0 && pb.info) {
-      pb.info->dt = dt;
-      pb.info->t += dt;
-      pb.info->steps += 1;
-    }
+  }
+  if (w.k == 0 && threadIdx.x == 0 && pb.info) {
+    pb.info->dt = dt;
+    pb.info->t += dt;
+    pb.info->steps += 1;
   }
 }
 
@@ -190,9 +176,10 @@ struct BCgArgs {
   int nitems_n, nprob;
   double *partials;       // [nitems_n][3]
   int *active;            // number of problems still iterating
-  GridBarrier *bar;
+  GridBarrier *bar;       // this launch's barrier (zero at launch)
+  GridBarrier *bar_next;  // the next launch's barrier, zeroed at the end of this one
   int *status;
-  int stage;              // 0 or 1: which cg_iters slot of the step records
+  int stage;              // 0 or 1: which cg_iters slot of the step records and which update
   double tol;
   int max_it;
 };
@@ -259,7 +246,14 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
   auto sync = [&]() { ++nbar; return grid_sync(A.bar, nbar * (unsigned long long)G, A.status); };
   const double tol2 = A.tol * A.tol;
 
-  // node phase helper: per node of the item (one thread per scalar node)
+  // ---- right-hand side: rhs = -(F.1) from the force pass's E-vector (read
+  // before the matvec below overwrites it); the solver count starts at zero
+  if (blockIdx.x == 0 && threadIdx.x == 0) *A.active = 0;
+  for (int it = blockIdx.x; it < A.nitems_n; it += G) {
+    const ItemN w = A.items_n[it];
+    node_rhs(A.probs[w.pid], w);
+  }
+  if (!sync()) return;
   // ---- init: E-vector of M a (a masked)
   for (int it = blockIdx.x; it < A.nitems_e; it += G) {
     const ItemE w = A.items_e[it];
@@ -441,6 +435,15 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
       if (sc.status) pb.info->status = sc.status;
     }
   }
+  if (!sync()) return;
+  // ---- the stage's node update with the solved accelerations
+  for (int it = blockIdx.x; it < A.nitems_n; it += G) {
+    const ItemN w = A.items_n[it];
+    if (A.stage == 0) node_mid(A.probs[w.pid], w);
+    else node_final(A.probs[w.pid], w);
+  }
+  // nothing waits on bar_next during this launch: the next launch starts from zero
+  if (blockIdx.x == 0 && threadIdx.x == 0) A.bar_next->count = 0ull;
 }
 
 }  // namespace
@@ -452,7 +455,11 @@ struct lh_batch {
   int n = 0;
   std::vector<lh_ctx *> ctx;
   std::vector<int> order;
-  int tiles[5] = {0, 1, 1, 1, 1};   // element batches per work item, per order (autotuned)
+  // tile shapes (autotuned): element batches per work item of the element passes
+  // and of the solver, per order, and the threads per block of the element passes
+  int tiles[5] = {0, 1, 1, 1, 1};
+  int tiles_cg[5] = {0, 1, 1, 1, 1};
+  int tpb = 256;
   char *arena = nullptr;
   size_t arena_bytes = 0;
   // device arrays
@@ -463,17 +470,19 @@ struct lh_batch {
   BScal *scal = nullptr;
   ItemE *items_e = nullptr, *items_cg = nullptr;
   ItemN *items_n = nullptr;
-  int n_items_e = 0, n_items_cg = 0, n_items_n = 0, cap_items_e = 0;
+  int n_items_e = 0, n_items_cg = 0, n_items_n = 0, cap_items_e = 0, cap_items_cg = 0;
   double *partials = nullptr, *dts = nullptr;
   int *active = nullptr, *status = nullptr;
-  GridBarrier *bar = nullptr;
-  int grid_e = 0, grid_n = 0, grid_cg = 0;
+  GridBarrier *bar = nullptr;   // two: one per stage's solver launch
+  int grid_e[3] = {0, 0, 0};    // per element block size 128, 256, 512
+  int grid_cg = 0;
   size_t smem_e = 0, smem_cg = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double graph_tol = -1.0;
   int graph_max_it = -1;
-  lh_step_info *graph_info = nullptr;
+  lh_step_info *infos = nullptr;
+  std::vector<double *> xs, vs, es;
   std::string err;
 };
 
@@ -506,7 +515,7 @@ static int nbc_of(int order) {
   }
 }
 
-// Element work items of all problems, sorted by order, `tiles[p]` batches of `nbf(p)` elements each.
+// Work items of all problems, sorted by order, `tiles[p]` batches of `nbf(p)` elements each.
 template <typename NBF>
 static std::vector<ItemE> make_items(const lh_batch *b, const int *tiles, NBF nbf) {
   std::vector<ItemE> items;
@@ -522,18 +531,28 @@ static std::vector<ItemE> make_items(const lh_batch *b, const int *tiles, NBF nb
 
 static lh_status upload_items(lh_batch *b) {
   std::vector<ItemE> ie = make_items(b, b->tiles, nb_of);
-  if ((int)ie.size() > b->cap_items_e) return bfail(b, LH_ERR_ARG, "work list larger than at creation");
+  std::vector<ItemE> ic = make_items(b, b->tiles_cg, nbc_of);
+  if ((int)ie.size() > b->cap_items_e || (int)ic.size() > b->cap_items_cg)
+    return bfail(b, LH_ERR_ARG, "work list larger than at creation");
   BCUDA(b, cudaMemcpy(b->items_e, ie.data(), ie.size() * sizeof(ItemE), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->items_cg, ic.data(), ic.size() * sizeof(ItemE), cudaMemcpyHostToDevice));
   b->n_items_e = (int)ie.size();
+  b->n_items_cg = (int)ic.size();
   return LH_OK;
+}
+
+static int tpb_index(int tpb) { return tpb == 128 ? 0 : (tpb == 512 ? 2 : 1); }
+
+static void drop_graph(lh_batch *b) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
 }
 
 extern "C" {
 
 void lh_batch_destroy(lh_batch *b) {
   if (!b) return;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  drop_graph(b);
   if (b->arena) cudaFree(b->arena);
   delete b;
 }
@@ -557,7 +576,11 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
     if (!(dt[i] > 0.0)) { lh_batch_destroy(b); return bfail(nullptr, LH_ERR_ARG, "dt must be > 0"); }
     b->ctx.push_back(c);
     b->order.push_back(c->p);
+    b->xs.push_back(x[i]);
+    b->vs.push_back(v[i]);
+    b->es.push_back(e[i]);
   }
+  b->infos = infos;
   // work lists (element items with the largest tile count used later must fit: size with tile 1)
   const int tiles1[5] = {0, 1, 1, 1, 1};
   std::vector<ItemE> ie = make_items(b, tiles1, nb_of);
@@ -603,7 +626,7 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
       {(void **)&b->scal, n * sizeof(BScal)},     {(void **)&b->items_e, nie * sizeof(ItemE)},
       {(void **)&b->items_cg, nic * sizeof(ItemE)}, {(void **)&b->items_n, nin * sizeof(ItemN)},
       {(void **)&b->partials, nin * 3 * sizeof(double)}, {(void **)&b->dts, n * sizeof(double)},
-      {(void **)&b->active, 64}, {(void **)&b->status, 64}, {(void **)&b->bar, 64}};
+      {(void **)&b->active, 64}, {(void **)&b->status, 64}, {(void **)&b->bar, 2 * sizeof(GridBarrier)}};
   size_t bytes = 0;
   for (auto &it : items) bytes += (it.bytes + 255) / 256 * 256;
   if (cudaMalloc(&b->arena, bytes) != cudaSuccess) {
@@ -680,6 +703,7 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
   b->n_items_e = (int)nie;
   b->cap_items_e = (int)nie;
   b->n_items_cg = (int)nic;
+  b->cap_items_cg = (int)nic;
   b->n_items_n = (int)nin;
   // launch shapes: shared memory = largest family's need
   b->smem_e = std::max({F2<1>::qdata_smem(), F2<2>::qdata_smem(), F2<3>::qdata_smem(), F2<4>::qdata_smem(),
@@ -687,51 +711,63 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
                         F2<1>::force_t_smem(), F2<2>::force_t_smem(), F2<3>::force_t_smem(),
                         F2<4>::force_t_smem()});
   b->smem_cg = std::max({F2<1>::cg_smem(), F2<2>::cg_smem(), F2<3>::cg_smem(), F2<4>::cg_smem()});
-  const void *ke[] = {(const void *)k_b_qdata, (const void *)k_b_force, (const void *)k_b_force_t};
   int sms = 0, dev = 0, occ = 0;
   BCUDA(b, cudaGetDevice(&dev));
   BCUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int occ_e = 1 << 30;
-  for (const void *k : ke) {
-    BCUDA(b, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_e));
-    BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, b->smem_e));
-    occ_e = std::min(occ_e, occ);
+  const void *ke[3][2] = {{(const void *)k_b_qf<128>, (const void *)k_b_force_t<128>},
+                          {(const void *)k_b_qf<256>, (const void *)k_b_force_t<256>},
+                          {(const void *)k_b_qf<512>, (const void *)k_b_force_t<512>}};
+  const int tpbs[3] = {128, 256, 512};
+  for (int t = 0; t < 3; ++t) {
+    int occ_e = 1 << 30;
+    for (const void *k : ke[t]) {
+      BCUDA(b, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_e));
+      BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, tpbs[t], b->smem_e));
+      occ_e = std::min(occ_e, occ);
+    }
+    b->grid_e[t] = std::max(1, occ_e) * sms;
   }
-  b->grid_e = std::max(1, occ_e) * sms;
   BCUDA(b, cudaFuncSetAttribute((const void *)k_b_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_cg));
   BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_b_cg, kThreadsCG, b->smem_cg));
   if (occ < 1) { lh_batch_destroy(b); return bfail(nullptr, LH_ERR_CUDA, "batched solver cannot be resident"); }
   b->grid_cg = std::min(occ, 2) * sms;
-  b->grid_n = 4 * sms;
   BCUDA(b, cudaDeviceSynchronize());
   *out = b;
   return LH_OK;
 }
 
 static lh_status enqueue_step(lh_batch *b, double tol, int max_it, cudaStream_t s) {
-  const int ge = b->grid_e, gn = b->grid_n;
+  const int ti = tpb_index(b->tpb), ge = b->grid_e[ti];
+  auto qf = [&](const QdataArgs *q) {
+    switch (b->tpb) {
+      case 128: k_b_qf<128><<<ge, 128, b->smem_e, s>>>(q, b->fa, b->items_e, b->n_items_e); break;
+      case 512: k_b_qf<512><<<ge, 512, b->smem_e, s>>>(q, b->fa, b->items_e, b->n_items_e); break;
+      default: k_b_qf<256><<<ge, 256, b->smem_e, s>>>(q, b->fa, b->items_e, b->n_items_e); break;
+    }
+  };
+  auto ft = [&](const ForceTArgs *t) {
+    switch (b->tpb) {
+      case 128: k_b_force_t<128><<<ge, 128, b->smem_e, s>>>(t, b->items_e, b->n_items_e); break;
+      case 512: k_b_force_t<512><<<ge, 512, b->smem_e, s>>>(t, b->items_e, b->n_items_e); break;
+      default: k_b_force_t<256><<<ge, 256, b->smem_e, s>>>(t, b->items_e, b->n_items_e); break;
+    }
+  };
   auto cg = [&](int stage) -> lh_status {
     BCgArgs a{b->probs, b->scal, b->items_cg, b->n_items_cg, b->items_n, b->n_items_n, b->n,
-              b->partials, b->active, b->bar, b->status, stage, tol, max_it};
-    BCUDA(b, cudaMemsetAsync(b->bar, 0, 64, s));
-    BCUDA(b, cudaMemsetAsync(b->active, 0, 64, s));
+              b->partials, b->active, b->bar + stage, b->bar + (1 - stage), b->status, stage, tol, max_it};
     void *args[] = {&a};
     BCUDA(b, cudaLaunchCooperativeKernel((const void *)k_b_cg, dim3(b->grid_cg), dim3(kThreadsCG), args,
                                          b->smem_cg, s));
     return LH_OK;
   };
-  k_b_qdata<<<ge, kThreads, b->smem_e, s>>>(b->q1, b->items_e, b->n_items_e);
-  k_b_force<<<ge, kThreads, b->smem_e, s>>>(b->fa, b->items_e, b->n_items_e);
-  k_b_rhs<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
+  // stage 1 at S_n: qdata + F.1, solve + rhs + mid update, F^T v + e update
+  qf(b->q1);
   if (lh_status st = cg(0)) return st;
-  k_b_mid<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
-  k_b_force_t<<<ge, kThreads, b->smem_e, s>>>(b->t1, b->items_e, b->n_items_e);
-  k_b_qdata<<<ge, kThreads, b->smem_e, s>>>(b->q2, b->items_e, b->n_items_e);
-  k_b_force<<<ge, kThreads, b->smem_e, s>>>(b->fa, b->items_e, b->n_items_e);
-  k_b_rhs<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
+  ft(b->t1);
+  // stage 2 at S_half
+  qf(b->q2);
   if (lh_status st = cg(1)) return st;
-  k_b_final<<<gn, kNodeItem, 0, s>>>(b->probs, b->items_n, b->n_items_n);
-  k_b_force_t<<<ge, kThreads, b->smem_e, s>>>(b->t2, b->items_e, b->n_items_e);
+  ft(b->t2);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("batched step launch: ") + cudaGetErrorString(e));
   return LH_OK;
@@ -743,8 +779,7 @@ lh_status lh_batch_step(lh_batch *b, double rel_tol, int max_it, lh_stream_t str
   if (max_it <= 0) max_it = 1000;
   cudaStream_t s = (cudaStream_t)stream;
   if (!b->exec || b->graph_tol != rel_tol || b->graph_max_it != max_it) {
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    drop_graph(b);
     cudaStream_t cap;
     BCUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     BCUDA(b, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -763,52 +798,141 @@ lh_status lh_batch_step(lh_batch *b, double rel_tol, int max_it, lh_stream_t str
   return LH_OK;
 }
 
-// Times the batched element kernels (stage-1 qdata, F.1, F^T v: none of them
-// changes the state) for tiles of 1, 2 and 4 element batches per work item,
-// one order at a time, and keeps the fastest tile per order. Synchronous.
-lh_status lh_batch_autotune(lh_batch *b, int *tiles_out) {
+static void get_config(const lh_batch *b, int *cfg) {
+  for (int p = 1; p <= 4; ++p) {
+    cfg[p - 1] = b->tiles[p];
+    cfg[3 + p] = b->tiles_cg[p];
+  }
+  cfg[8] = b->tpb;
+}
+
+lh_status lh_batch_set_config(lh_batch *b, const int *cfg) {
+  if (!b || !cfg) return LH_ERR_ARG;
+  for (int k = 0; k < 8; ++k)
+    if (cfg[k] != 1 && cfg[k] != 2 && cfg[k] != 4) return bfail(b, LH_ERR_ARG, "tiles must be 1, 2 or 4");
+  if (cfg[8] != 128 && cfg[8] != 256 && cfg[8] != 512)
+    return bfail(b, LH_ERR_ARG, "threads per block must be 128, 256 or 512");
+  for (int p = 1; p <= 4; ++p) {
+    b->tiles[p] = cfg[p - 1];
+    b->tiles_cg[p] = cfg[3 + p];
+  }
+  b->tpb = cfg[8];
+  if (lh_status st = upload_items(b)) return st;
+  drop_graph(b);   // the captured step holds the old work lists and launch shapes
+  return LH_OK;
+}
+
+// Autotuner: times whole batched steps (both element passes and the solver) for
+// candidate tile shapes and keeps, coordinate by coordinate, every change that
+// makes the step at least 1 % faster: per order the element tile (1, 2, 4
+// batches per work item) and the solver tile (1, 2), then the element passes'
+// threads per block (128, 256, 512). Every candidate starts from the same state
+// (x, v, e, the accelerations that warm-start the solves and the step records
+// are saved first and restored after each trial and at the end), so the
+// problems are left exactly as they were. Synchronous; allocates and frees one
+// snapshot buffer.
+lh_status lh_batch_autotune(lh_batch *b, int *cfg_out) {
   if (!b) return LH_ERR_ARG;
-  cudaEvent_t e0, e1;
-  BCUDA(b, cudaEventCreate(&e0));
-  BCUDA(b, cudaEventCreate(&e1));
-  auto time_kernels = [&]() -> float {
+  // snapshot of everything a step changes
+  struct Seg { double *p; size_t n; };
+  std::vector<Seg> segs;
+  for (int i = 0; i < b->n; ++i) {
+    const lh_ctx *c = b->ctx[i];
+    const size_t nv = (size_t)2 * c->mesh.nh1, nl = (size_t)c->mesh.ne * c->p * c->p;
+    segs.push_back({b->xs[i], nv});
+    segs.push_back({b->vs[i], nv});
+    segs.push_back({b->es[i], nl});
+    segs.push_back({c->a_prev, nv});
+  }
+  size_t total = 0;
+  for (auto &g : segs) total += g.n;
+  const size_t info_bytes = b->infos ? (size_t)b->n * sizeof(lh_step_info) : 0;
+  char *snap = nullptr;
+  BCUDA(b, cudaMalloc(&snap, total * sizeof(double) + info_bytes));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  lh_status result = LH_OK;
+  auto copy_all = [&](bool save) -> cudaError_t {
+    size_t off = 0;
+    for (auto &g : segs) {
+      double *d = (double *)snap + off;
+      const cudaError_t e = save ? cudaMemcpy(d, g.p, g.n * sizeof(double), cudaMemcpyDeviceToDevice)
+                                 : cudaMemcpy(g.p, d, g.n * sizeof(double), cudaMemcpyDeviceToDevice);
+      if (e != cudaSuccess) return e;
+      off += g.n;
+    }
+    if (info_bytes) {
+      char *d = snap + total * sizeof(double);
+      return save ? cudaMemcpy(d, b->infos, info_bytes, cudaMemcpyDeviceToDevice)
+                  : cudaMemcpy(b->infos, d, info_bytes, cudaMemcpyDeviceToDevice);
+    }
+    return cudaSuccess;
+  };
+  // one trial: restore, one warm-up step (captures the graph), three timed steps
+  auto trial = [&](float *ms_out) -> lh_status {
+    cudaError_t e = copy_all(false);
+    if (e != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(e));
+    if (lh_status st = lh_batch_step(b, 1e-12, 1000, nullptr)) return st;
     float best = 1e30f;
     for (int r = 0; r < 3; ++r) {
       cudaEventRecord(e0);
-      k_b_qdata<<<b->grid_e, kThreads, b->smem_e>>>(b->q1, b->items_e, b->n_items_e);
-      k_b_force<<<b->grid_e, kThreads, b->smem_e>>>(b->fa, b->items_e, b->n_items_e);
-      k_b_force_t<<<b->grid_e, kThreads, b->smem_e>>>(b->t1, b->items_e, b->n_items_e);
+      if (lh_status st = lh_batch_step(b, 1e-12, 1000, nullptr)) return st;
       cudaEventRecord(e1);
-      cudaEventSynchronize(e1);
+      e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("autotune step: ") + cudaGetErrorString(e));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       best = std::min(best, ms);
     }
-    return best;
+    int st_host = 0;
+    e = cudaMemcpy(&st_host, b->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("autotune status: ") + cudaGetErrorString(e));
+    if (st_host) return bfail(b, (lh_status)st_host, "autotune: a batched step latched a device error");
+    *ms_out = best;
+    return LH_OK;
   };
-  for (int p = 1; p <= 4; ++p) {
-    bool present = false;
-    for (int o : b->order) present |= o == p;
-    if (!present) continue;
-    int best_tile = b->tiles[p];
-    float best_t = 1e30f;
-    for (int tile : {1, 2, 4}) {
-      b->tiles[p] = tile;
-      if (lh_status st = upload_items(b)) return st;
-      const float t = time_kernels();
-      if (t < best_t) { best_t = t; best_tile = tile; }
+  int cfg[9];
+  do {
+    cudaError_t e = copy_all(true);
+    if (e != cudaSuccess) { result = bfail(b, LH_ERR_CUDA, std::string("autotune snapshot: ") + cudaGetErrorString(e)); break; }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      result = bfail(b, LH_ERR_CUDA, "autotune: cudaEventCreate failed");
+      break;
     }
-    b->tiles[p] = best_tile;
-    if (lh_status st = upload_items(b)) return st;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  BCUDA(b, cudaGetLastError());
-  if (tiles_out)
-    for (int p = 1; p <= 4; ++p) tiles_out[p - 1] = b->tiles[p];
-  // the captured step graph (if any) holds the old work-list length
-  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    get_config(b, cfg);
+    float best = 0.f;
+    if ((result = trial(&best)) != LH_OK) break;
+    auto try_cfg = [&](int k, int val) -> lh_status {
+      int cand[9];
+      std::memcpy(cand, cfg, sizeof(cand));
+      if (cand[k] == val) return LH_OK;
+      cand[k] = val;
+      if (lh_status st = lh_batch_set_config(b, cand)) return st;
+      float t = 0.f;
+      if (lh_status st = trial(&t)) return st;
+      if (t < 0.99f * best) {
+        best = t;
+        std::memcpy(cfg, cand, sizeof(cand));
+      }
+      return lh_batch_set_config(b, cfg);
+    };
+    for (int p = 1; p <= 4 && result == LH_OK; ++p) {
+      bool present = false;
+      for (int o : b->order) present |= o == p;
+      if (!present) continue;
+      for (int t : {2, 4})
+        if ((result = try_cfg(p - 1, t)) != LH_OK) break;
+      if (result == LH_OK) result = try_cfg(3 + p, 2);
+    }
+    for (int t : {128, 512})
+      if (result == LH_OK) result = try_cfg(8, t);
+  } while (false);
+  const cudaError_t er = copy_all(false);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(snap);
+  if (result != LH_OK) return result;
+  if (er != cudaSuccess) return bfail(b, LH_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(er));
+  if (cfg_out) get_config(b, cfg_out);
   return LH_OK;
 }
 

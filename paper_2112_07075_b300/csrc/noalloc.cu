@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "lh_internal.h"
 
@@ -14,11 +15,14 @@ namespace {
 
 // Maximum scratch: 32 MiB of element-vector data (dim * NE * (p+1)^dim doubles).
 constexpr size_t kScratchDoubles = (size_t(32) << 20) / sizeof(double);
+// Basis tables of every compiled (order, q1) pair, one fixed slot each.
 constexpr int kTabDoubles = 512;
+constexpr int kFamilies[][2] = {{1, 2}, {2, 3}, {2, 4}, {3, 6}, {4, 6}, {4, 8}};
+constexpr int kNumFamilies = sizeof(kFamilies) / sizeof(kFamilies[0]);
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
-static __device__ __align__(256) double g_tab[kTabDoubles];
+static __device__ __align__(256) double g_tab[kNumFamilies * kTabDoubles];
 
 // Device addresses of the two arrays, looked up once per device. In host code
 // g_scratch / g_tab are only host-side stand-ins for the symbols and must never
@@ -35,6 +39,47 @@ lh_status fail(lh_status s, const std::string &msg) {
   return s;
 }
 
+int family_slot(int order, int q1) {
+  for (int k = 0; k < kNumFamilies; ++k)
+    if (kFamilies[k][0] == order && kFamilies[k][1] == q1) return k;
+  return -1;
+}
+
+// One-time set-up of the current device (caller holds g_mu): resolve the arrays'
+// device addresses, upload the basis tables of every family into their slots
+// (synchronous copy, then a device synchronisation so that later calls on any
+// stream see the tables), and raise the dynamic shared-memory limit of every
+// compiled mass kernel. After this, calls only launch kernels.
+lh_status setup_device(int dev) {
+  void *ps = nullptr, *pt = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ps, g_scratch);
+  if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+  e = cudaGetSymbolAddress(&pt, g_tab);
+  if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("cudaGetSymbolAddress(tab): ") + cudaGetErrorString(e));
+  std::vector<double> tabs((size_t)kNumFamilies * kTabDoubles, 0.0);
+  for (int k = 0; k < kNumFamilies; ++k) {
+    if (lh::table_length(kFamilies[k][0], kFamilies[k][1]) > kTabDoubles)
+      return fail(LH_ERR_ARG, "lh_mass_mult_noalloc: basis table too large");
+    lh::build_tables(kFamilies[k][0], kFamilies[k][1], tabs.data() + (size_t)k * kTabDoubles, kTabDoubles);
+  }
+  e = cudaMemcpy(pt, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  for (int k = 0; k < kNumFamilies; ++k) {
+    for (int dim = 2; dim <= 3; ++dim) {
+      const lh::Ops *ops = dim == 2 ? lh::find_ops_2d(kFamilies[k][0], kFamilies[k][1])
+                                    : lh::find_ops_3d(kFamilies[k][0], kFamilies[k][1]);
+      if (!ops) continue;
+      e = cudaFuncSetAttribute(ops->k_mass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ops->smem_mass);
+      if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    }
+  }
+  g_addrs[dev].scratch = (double *)ps;
+  g_addrs[dev].tab = (double *)pt;
+  return LH_OK;
+}
+
 }  // namespace
 
 extern "C" lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int order, int q1, const double *mq,
@@ -46,7 +91,9 @@ extern "C" lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int o
   if (!mq || !x || !y) return fail(LH_ERR_ARG, "lh_mass_mult_noalloc: null pointer");
   if (x == y) return fail(LH_ERR_ARG, "lh_mass_mult_noalloc: x and y must not alias");
   const lh::Ops *ops = dim == 2 ? lh::find_ops_2d(order, q1) : lh::find_ops_3d(order, q1);
-  if (!ops) return fail(LH_ERR_UNSUPPORTED, "lh_mass_mult_noalloc: no compiled kernels for this (dim, order, q1)");
+  const int slot = family_slot(order, q1);
+  if (!ops || slot < 0)
+    return fail(LH_ERR_UNSUPPORTED, "lh_mass_mult_noalloc: no compiled kernels for this (dim, order, q1)");
   if (dim == 2) nz = 1;
   const double ne_d = (double)nx * ny * nz;
   int nd = 1;
@@ -57,8 +104,6 @@ extern "C" lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int o
                                 " bytes of element-vector scratch; the static maximum is " +
                                 std::to_string((long long)kScratchDoubles * 8) + " bytes (32 MiB)");
   }
-  const int tablen = lh::table_length(order, q1);
-  if (tablen > kTabDoubles) return fail(LH_ERR_ARG, "lh_mass_mult_noalloc: basis table too large");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -66,18 +111,10 @@ extern "C" lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int o
   if (dev < 0 || dev >= kMaxDevices) return fail(LH_ERR_ARG, "lh_mass_mult_noalloc: device index too large");
   DevAddrs addrs;
   {
-    // One-time set-up per device (the current one): resolve the symbols' device addresses.
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_addrs[dev].scratch) {
-      void *ps = nullptr, *pt = nullptr;
-      e = cudaGetSymbolAddress(&ps, g_scratch);
-      if (e != cudaSuccess)
-        return fail(LH_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-      e = cudaGetSymbolAddress(&pt, g_tab);
-      if (e != cudaSuccess)
-        return fail(LH_ERR_CUDA, std::string("cudaGetSymbolAddress(tab): ") + cudaGetErrorString(e));
-      g_addrs[dev].scratch = (double *)ps;
-      g_addrs[dev].tab = (double *)pt;
+      const lh_status st = setup_device(dev);
+      if (st != LH_OK) return st;
     }
     addrs = g_addrs[dev];
   }
@@ -93,16 +130,9 @@ extern "C" lh_status lh_mass_mult_noalloc(int dim, int nx, int ny, int nz, int o
   m.nh1 = m.n1x * m.n1y * m.n1z;
   cudaStream_t s = (cudaStream_t)stream;
 
-  double tab[kTabDoubles];
-  lh::build_tables(order, q1, tab, kTabDoubles);
-  e = cudaMemcpyAsync(addrs.tab, tab, tablen * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
-  e = cudaFuncSetAttribute(ops->k_mass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ops->smem_mass);
-  if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-
   // Every element writes all of its scratch entries before the gather reads
   // them, so no part of the scratch has to start at zero.
-  lh::MassArgs a{m, addrs.tab, mq, x, addrs.scratch};
+  lh::MassArgs a{m, addrs.tab + (size_t)slot * kTabDoubles, mq, x, addrs.scratch};
   ops->mass(a, (m.ne + ops->nb - 1) / ops->nb, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LH_ERR_CUDA, std::string("mass kernel: ") + cudaGetErrorString(e));

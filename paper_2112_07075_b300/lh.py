@@ -26,7 +26,8 @@ PRECISIONS = {"fp64": 0, "fp32_ir": 1, "bf16tc_ir": 2}
 EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_status", "lh_init_state",
             "lh_update_qdata", "lh_copy_qdata", "lh_force_mult", "lh_force_mult_t", "lh_mass_mult",
             "lh_mass_cg", "lh_energy_solve", "lh_rk2avg_step", "lh_mass_mult_noalloc",
-            "lh_batch_create", "lh_batch_autotune", "lh_batch_step", "lh_batch_last_error", "lh_batch_destroy",
+            "lh_batch_create", "lh_batch_autotune", "lh_batch_set_config", "lh_batch_step", "lh_batch_last_error",
+            "lh_batch_destroy",
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_sync_status",
             "lh_learn_attach",
@@ -103,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP),
                                 ctypes.POINTER(D), VP, ctypes.POINTER(P)]),
         "lh_batch_autotune": (I, [P, ctypes.POINTER(I)]),
+        "lh_batch_set_config": (I, [P, ctypes.POINTER(I)]),
         "lh_batch_step": (I, [P, D, I, VP]),
         "lh_batch_last_error": (ctypes.c_char_p, [P]),
         "lh_batch_destroy": (None, [P]),
@@ -182,8 +184,19 @@ def mass_mult_noalloc(dim, n, order, q1, mq, x, y):
 
     For callers that may not allocate device memory: mq ([NE][q1^dim] quadrature
     data omega*rho0*detJ0), x and y are caller-owned CUDA tensors."""
+    import torch
     lib = load_library()
     nx, ny, nz = (n, n, n if dim == 3 else 1) if np.isscalar(n) else (tuple(n) + (1,))[:3]
+    if dim == 2:
+        nz = 1
+    ne = nx * ny * nz
+    n_h1 = (nx * order + 1) * (ny * order + 1) * ((nz * order + 1) if dim == 3 else 1)
+    # the C ABI takes bare pointers: every length is checked here, before the call
+    for name, t, need in (("mq", mq, ne * q1 ** dim), ("x", x, dim * n_h1), ("y", y, dim * n_h1)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError(f"mass_mult_noalloc: {name} must be a contiguous float64 CUDA tensor")
+        if t.numel() < need:
+            raise ValueError(f"mass_mult_noalloc: {name} has {t.numel()} values, needs {need}")
     st = lib.lh_mass_mult_noalloc(dim, nx, ny, nz, order, q1, _ptr(mq), _ptr(x), _ptr(y), _stream())
     if st != LH_OK:
         raise LhError(st, lib.lh_last_error(None).decode())
@@ -403,10 +416,19 @@ class Batch:
         if st != LH_OK:
             raise LhError(st, self.lib.lh_batch_last_error(self.h).decode())
 
+    @staticmethod
+    def _cfg_dict(c):
+        return {"tiles": list(c[0:4]), "tiles_cg": list(c[4:8]), "threads": int(c[8])}
+
     def autotune(self):
-        tiles = (ctypes.c_int * 4)()
-        self._check(self.lib.lh_batch_autotune(self.h, tiles))
-        return list(tiles)
+        """Pick the tile shapes by timing whole steps (the state is left unchanged)."""
+        cfg = (ctypes.c_int * 9)()
+        self._check(self.lib.lh_batch_autotune(self.h, cfg))
+        return self._cfg_dict(cfg)
+
+    def set_config(self, tiles=(1, 1, 1, 1), tiles_cg=(1, 1, 1, 1), threads=256):
+        cfg = (ctypes.c_int * 9)(*(list(tiles) + list(tiles_cg) + [int(threads)]))
+        self._check(self.lib.lh_batch_set_config(self.h, cfg))
 
     def step(self, rel_tol=1e-12, max_it=1000):
         self._check(self.lib.lh_batch_step(self.h, float(rel_tol), int(max_it), _stream()))

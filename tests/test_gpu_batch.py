@@ -48,8 +48,8 @@ def test_batched_steps_match_unbatched_and_oracle():
             rctx.rk2avg_step(x, v, e, dt, info)
         refs.append((x, v, e, rctx))
     batch = Batch(ctxs, states, [dt] * len(ctxs))
-    tiles = batch.autotune()
-    assert all(t in (1, 2, 4) for t in tiles)
+    cfg = batch.autotune()
+    assert all(t in (1, 2, 4) for t in cfg["tiles"] + cfg["tiles_cg"]) and cfg["threads"] in (128, 256, 512)
     for _ in range(steps):
         batch.step()
     torch.cuda.synchronize()
@@ -74,3 +74,68 @@ def test_batched_steps_match_unbatched_and_oracle():
             a = a.cpu().numpy()
             assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b)
     batch.close()
+
+
+def test_configured_256_problem_batch_matches_one_by_one_and_oracle():
+    """The batching workload as configured: 256 problems from generator seed 4 (orders 1-4,
+    n in [8, 64], half Taylor-Green, half Gresho), fixed dt_k = 0.5 dt_est_k(S0), 20 steps.
+    Every problem against its own lh_rk2avg_step run (1e-12 per field); the smallest
+    problem of each (order, kind) against the oracle (1e-11 per field)."""
+    from paper_2112_07075_b300.lh import Batch, Context
+    probs = inputs.batch_problems(4)
+    steps = 20
+    ctxs, states, refs, dts = [], [], [], []
+    est = torch.zeros(len(probs), dtype=torch.float64, device="cuda")
+    for i, pr in enumerate(probs):
+        ctx, V, src = _make(pr)
+        x, v, e = ctx.init_state(pr["kind"])
+        ctx.update_qdata(x, v, e, est[i:i + 1])
+        ctxs.append(ctx)
+        states.append((x, v, e))
+    dts = (0.5 * est).cpu().tolist()
+    assert all(d > 0 for d in dts)
+    for i, pr in enumerate(probs):
+        rctx, _, _ = _make(pr)
+        x, v, e = rctx.init_state(pr["kind"])
+        info = rctx.new_step_info()
+        for _ in range(steps):
+            rctx.rk2avg_step(x, v, e, dts[i], info)
+        refs.append(tuple(t.cpu().numpy() for t in (x, v, e)))
+        assert rctx.read_step_info(info).status == 0
+        rctx.close()
+    batch = Batch(ctxs, states, dts)
+    batch.autotune()
+    for _ in range(steps):
+        batch.step()
+    torch.cuda.synchronize()
+    infos = batch.read_infos()
+    worst = 0.0
+    for i in range(len(probs)):
+        assert infos[i].steps == steps and infos[i].status == 0, i
+        assert max(infos[i].cg_rel_res) <= 1e-12
+        for a, b in zip(states[i], refs[i]):
+            a = a.cpu().numpy()
+            err = np.linalg.norm(a - b) / np.linalg.norm(b)
+            worst = max(worst, err)
+            assert err <= 1e-12, (i, probs[i], err)
+    # oracle: the smallest problem of every (order, kind)
+    picks = {}
+    for i, pr in enumerate(probs):
+        key = (pr["order"], pr["kind"])
+        if key not in picks or pr["n"] < probs[picks[key]]["n"]:
+            picks[key] = i
+    for i in sorted(picks.values()):
+        pr = probs[i]
+        hy = Hydro(Params(dim=2, n=pr["n"], order=pr["order"], q1=2 * pr["order"],
+                          vertices=inputs.box_vertices(2, pr["n"], pr["lo"], pr["hi"]),
+                          source="tg2d" if pr["kind"] == "taylor_green" else "none"))
+        xo, vo, eo = hy.initial_state(pr["kind"])
+        for _ in range(steps):
+            xo, vo, eo, _ = hy.rk2avg_step(xo, vo, eo, dt=dts[i])
+        for a, b in zip(states[i], (xo, vo, eo)):
+            a = a.cpu().numpy().reshape(-1)
+            b = b.reshape(-1)
+            assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(b), (i, pr)
+    batch.close()
+    for c in ctxs:
+        c.close()

@@ -6,7 +6,10 @@ owns all device memory through its own pool. lh_mass_mult_noalloc serves them:
 it needs no context and keeps its element-vector scratch in a fixed 32 MiB static
 device array. These tests call it through the C ABI and check that two calls in a
 row give the same y = M_v x as the context-based lh_mass_mult, within the
-per-operation tolerance the other GPU tests use.
+per-operation tolerance the other GPU tests use; that a later call leaves the
+device's free memory unchanged (it allocates nothing); that a small case agrees
+with the oracle's assembled mass matrix; and that the binding rejects tensors of
+the wrong type or length before anything reaches the C ABI.
 
 The file name makes pytest collect it last, so a run that stops at the first
 failure has already run every other test.
@@ -17,6 +20,7 @@ import numpy as np
 import pytest
 
 from oracle.fem import Tables, jacobians
+from oracle.hydro import Hydro, Params
 from oracle.mesh import Mesh
 from paper_2112_07075_b300 import inputs, lh
 
@@ -46,7 +50,37 @@ def test_noalloc_mass_mult_matches_context_on_two_calls_in_a_row():
         torch.cuda.synchronize()
         err = float((y - y_ref).abs().max() / y_ref.abs().max())
         assert err < OP_TOL, (call, err)
+        # a later call allocates nothing: the device's free memory is unchanged
+        free0 = torch.cuda.mem_get_info()[0]
+        y2 = torch.full_like(y_ref, float("nan"))
+        lh.mass_mult_noalloc(dim, n, p, q1, mq, x, y2)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.equal(y2, y)
         ctx.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_mass_mult_matches_oracle_assembled_mass():
+    torch = pytest.importorskip("torch")
+    dim, n, p, q1 = 2, 3, 2, 3
+    V = inputs.box_vertices(dim, n, jitter=0.15, seed=41)
+    hy = Hydro(Params(dim=dim, n=n, order=p, q1=q1, vertices=V))
+    u = inputs.uniform(42, (dim, hy.mesh.NH1))
+    ref = hy.mass_mult(u)
+    mq = torch.from_numpy(np.ascontiguousarray(_mass_qdata(dim, n, p, q1, V))).cuda()
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    lh.mass_mult_noalloc(dim, n, p, q1, mq, x, y)
+    torch.cuda.synchronize()
+    err = float(np.max(np.abs(y.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    assert err < OP_TOL
+    with pytest.raises(ValueError):
+        lh.mass_mult_noalloc(dim, n, p, q1, mq.float(), x, y)
+    with pytest.raises(ValueError):
+        lh.mass_mult_noalloc(dim, n, p, q1, mq, x[:, :-1].contiguous(), y)
+    with pytest.raises(ValueError):
+        lh.mass_mult_noalloc(dim, n, p, q1, mq[:-1], x, y)
 
 
 def test_noalloc_rejects_meshes_beyond_the_static_scratch():
