@@ -499,12 +499,19 @@ lh_status lh_mlp_sync_status(lh_mlp *m);
  * training example per element at every mass solve of lh_rk2avg_step that has
  * three earlier solutions (features into X_buf[row][586], targets into
  * T_buf[row][192], DEVICE, until capacity_rows rows are filled). mode 2: predict
- * the initial guess with `mlp`: the guess g and the previous solution are
- * compared by the Jacobi-preconditioned residual norm (r, D^-1 r), r = b - M .
- * (FP32 mass action, FP64 sums), and the smaller starts CG; CG still runs to its
- * tolerance (either precision). mode 0: detach.
+ * the initial guess with `mlp`: the guess g and the previous solution a_1 are
+ * compared by the Jacobi-preconditioned residual norm (r, D^-1 r): r = b - M g
+ * (FP32 mass action, FP64 sums) for the guess, r = b - b_prev for a_1 (the mass
+ * matrix is constant in time and a_1 solved the previous right-hand side b_prev
+ * to the CG tolerance); the smaller starts CG; CG still runs to its tolerance
+ * (either precision). mode 0: detach.
  * Allocates the form's device buffers (a set-up call); synchronous. */
 lh_status lh_learn_attach(lh_ctx *ctx, lh_mlp *mlp, int mode, float *X_buf, float *T_buf, int capacity_rows);
+/* Recording mode keeps every stride-th element of each solve (a rotating subset:
+ * solve k records elements e = (k mod stride) + j * stride), so long runs on large
+ * meshes fit the example buffer; default 1 (every element). LH_ERR_ARG without an
+ * attached learned form or for stride < 1. */
+lh_status lh_learn_set_record_stride(lh_ctx *ctx, int stride);
 /* HOST counters of the attached learned form: rows recorded, mass solves seen,
  * predictions made, predictions that won the residual comparison, and the mean
  * over predictions of the ratio of the two compared norms, learned over previous

@@ -13,9 +13,15 @@
 // Successive solutions differ by a small fraction of their size, so the history
 // enters as normalised differences: raw solutions rounded to BF16 would lose it.
 // In prediction mode the Jacobi-preconditioned residual norms (r, D^-1 r) of g and
-// a_1 are compared (FP32 mass action, FP64 sums) and the smaller one's vector
-// starts CG; the CG tolerance is unchanged, so the guess only changes the
-// iteration count.
+// a_1 are compared and the smaller one's vector starts CG; the CG tolerance is
+// unchanged, so the guess only changes the iteration count. The residual of g
+// takes one FP32 mass action; that of a_1 needs none: the mass matrix does not
+// change between solves (rho|J| = rho0|J0|) and a_1 solved the previous system to
+// the CG tolerance, so b - M a_1 = (b - b_prev) + O(tol |b_prev|) with b_prev the
+// previous right-hand side.
+// Recording mode can keep every k-th element of each solve (a rotating subset:
+// element e = o + j k with o = solve count mod k), so long runs on large meshes
+// fit a bounded example buffer.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -73,26 +79,30 @@ __global__ void k_scale_final(int nb, const double *__restrict__ part, double *_
 
 // History features: X[e][c*64 + i] = a_1 / s, X[e][192 + c*64 + i] = (a_1 - a_2) / s_d,
 // X[e][384 + c*64 + i] = (a_2 - a_3) / s_d at node(e, i), component c.
-__global__ void k_hist_features(MeshDesc m, const double *__restrict__ h0, const double *__restrict__ h1,
-                                const double *__restrict__ h2, const double *__restrict__ s, float *__restrict__ X) {
-  const size_t total = (size_t)m.ne * 576;
+// Row r of X holds element e = off + r * stride (stride 1, off 0: every element).
+__global__ void k_hist_features(MeshDesc m, int rows, int stride, int off, const double *__restrict__ h0,
+                                const double *__restrict__ h1, const double *__restrict__ h2,
+                                const double *__restrict__ s, float *__restrict__ X) {
+  const size_t total = (size_t)rows * 576;
   const double is = 1.0 / s[0], isd = 1.0 / s[1];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int e = (int)(t / 576), f = (int)(t % 576);
+    const int r = (int)(t / 576), f = (int)(t % 576);
+    const int e = off + r * stride;
     const int k = f / 192, c = (f / 64) % 3, i = f % 64;
     const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
     double val;
     if (k == 0) val = h0[gi] * is;
     else if (k == 1) val = (h0[gi] - h1[gi]) * isd;
     else val = (h1[gi] - h2[gi]) * isd;
-    X[(size_t)e * kIn + f] = (float)val;
+    X[(size_t)r * kIn + f] = (float)val;
   }
 }
 
 // Jacobian features at the element centroid: 9 entries of J / (h0 p) and det J / (h0 p)^3.
-__global__ void k_jac_features(MeshDesc m, const double *__restrict__ x, Cent cb, double hs,
-                               float *__restrict__ X) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.ne; e += gridDim.x * blockDim.x) {
+__global__ void k_jac_features(MeshDesc m, int rows, int stride, int off, const double *__restrict__ x, Cent cb,
+                               double hs, float *__restrict__ X) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int e = off + r * stride;
     const int base = h1_base<3, D>(m, e);
     double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = 0; i < ND; ++i) {
@@ -110,19 +120,20 @@ __global__ void k_jac_features(MeshDesc m, const double *__restrict__ x, Cent cb
     }
     const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
                        J[2] * (J[3] * J[7] - J[4] * J[6]);
-    float *out = X + (size_t)e * kIn + 576;
+    float *out = X + (size_t)r * kIn + 576;
     for (int k = 0; k < 9; ++k) out[k] = (float)(J[k] / hs);
     out[9] = (float)(det / (hs * hs * hs));
   }
 }
 
 // Targets: T[e][c*64 + i] = (a_new - a_1)[c][node(e,i)] / s_d.
-__global__ void k_targets(MeshDesc m, const double *__restrict__ anew, const double *__restrict__ a1,
-                          const double *__restrict__ s, float *__restrict__ T) {
-  const size_t total = (size_t)m.ne * kOut;
+__global__ void k_targets(MeshDesc m, int rows, int stride, int off, const double *__restrict__ anew,
+                          const double *__restrict__ a1, const double *__restrict__ s, float *__restrict__ T) {
+  const size_t total = (size_t)rows * kOut;
   const double is = 1.0 / s[1];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int e = (int)(t / kOut), f = (int)(t % kOut);
+    const int r = (int)(t / kOut), f = (int)(t % kOut);
+    const int e = off + r * stride;
     const int c = f / 64, i = f % 64;
     const size_t k = (size_t)c * m.nh1 + h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
     T[t] = (float)((anew[k] - a1[k]) * is);
@@ -145,46 +156,42 @@ __global__ void k_assemble(MeshDesc m, const float *__restrict__ Y, const double
   }
 }
 
-// FP32 E-vectors of M g (evA) and M a_1 (evB) for the residual comparison.
+// FP32 E-vector of M g for the residual comparison.
 __global__ void __launch_bounds__(F::THREADS) k_resid_elem(MeshDesc m, const double *__restrict__ tab,
                                                            const float *__restrict__ mq32, const double *__restrict__ g,
-                                                           const double *__restrict__ a1, const double *__restrict__ idg,
-                                                           float *__restrict__ evA, float *__restrict__ evB) {
+                                                           const double *__restrict__ idg, float *__restrict__ evA) {
   constexpr int CX = F::CX, NQ = F::NQ, Q = 6;
   constexpr int MS = F::M_S;
   extern __shared__ double smd[];
   float *tb = (float *)smd, *tbt = tb + Q * D, *u = tbt + Q * D, *S = u + CX * ND, *uq = S + MS, *y = uq + CX * NQ;
   for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x) tb[k] = (float)tab[k < Q * D ? F::oB + k : F::oBt + k - Q * D];
   const int e0 = blockIdx.x * F::NB, nb = min(F::NB, m.ne - e0);
-  for (int pass = 0; pass < 2; ++pass) {
-    const double *src = pass == 0 ? g : a1;
-    float *ev = pass == 0 ? evA : evB;
-    __syncthreads();
-    for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
-      const int i = k % ND, bc = k / ND, c = bc % 3, b = bc / 3;
-      float val = 0.0f;
-      if (b < nb) {
-        const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e0 + b) + h1_local<3, D>(m, i);
-        val = idg[gi] != 0.0 ? (float)src[gi] : 0.0f;
-      }
-      u[k] = val;
+  for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
+    const int i = k % ND, bc = k / ND, c = bc % 3, b = bc / 3;
+    float val = 0.0f;
+    if (b < nb) {
+      const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e0 + b) + h1_local<3, D>(m, i);
+      val = idg[gi] != 0.0 ? (float)g[gi] : 0.0f;
     }
-    __syncthreads();
-    interp<3, D, Q, CX>(u, uq, S, tb);
-    for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
-      const int q = k % NQ, b = (k / NQ) / 3;
-      uq[k] *= b < nb ? mq32[(size_t)(e0 + b) * NQ + q] : 0.0f;
-    }
-    __syncthreads();
-    interp<3, Q, D, CX>(uq, y, S, tbt);
-    for (int k = threadIdx.x; k < nb * 3 * ND; k += blockDim.x) ev[(size_t)e0 * 3 * ND + k] = y[k];
+    u[k] = val;
   }
+  __syncthreads();
+  interp<3, D, Q, CX>(u, uq, S, tb);
+  for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
+    const int q = k % NQ, b = (k / NQ) / 3;
+    uq[k] *= b < nb ? mq32[(size_t)(e0 + b) * NQ + q] : 0.0f;
+  }
+  __syncthreads();
+  interp<3, Q, D, CX>(uq, y, S, tbt);
+  for (int k = threadIdx.x; k < nb * 3 * ND; k += blockDim.x) evA[(size_t)e0 * 3 * ND + k] = y[k];
 }
 
-// Preconditioned residual norms (r, D^-1 r) of both candidates -- the quantity
-// Jacobi-PCG itself reduces -- as per-block partials (FP64 sums of FP32 residuals).
-__global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const double *__restrict__ idg,
-                              const float *__restrict__ evA, const float *__restrict__ evB, double *__restrict__ part) {
+// Preconditioned residual norms (r, D^-1 r) -- the quantity Jacobi-PCG itself
+// reduces -- of both candidates as per-block partials: r_g = b - M g (FP32 action,
+// FP64 sums) and r_1 = b - b_prev for the previous solution a_1.
+__global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const double *__restrict__ bprev,
+                              const double *__restrict__ idg, const float *__restrict__ evA,
+                              double *__restrict__ part) {
   double acc[2] = {0.0, 0.0};
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < m.nh1; n += gridDim.x * blockDim.x) {
     int off[8];
@@ -192,10 +199,10 @@ __global__ void k_resid_nodes(MeshDesc m, const double *__restrict__ b, const do
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * m.nh1 + n;
       if (idg[k] == 0.0) continue;
-      float ma = 0.0f, mb = 0.0f;
-      for (int j = 0; j < cnt; ++j) { ma += evA[off[j] + c * ND]; mb += evB[off[j] + c * ND]; }
-      const double ra = b[k] - (double)ma, rb = b[k] - (double)mb;
-      acc[0] = fma(ra * idg[k], ra, acc[0]);   // Jacobi-preconditioned residual norms (r, D^-1 r)
+      float ma = 0.0f;
+      for (int j = 0; j < cnt; ++j) ma += evA[off[j] + c * ND];
+      const double ra = b[k] - (double)ma, rb = b[k] - bprev[k];
+      acc[0] = fma(ra * idg[k], ra, acc[0]);
       acc[1] = fma(rb * idg[k], rb, acc[1]);
     }
   }
@@ -242,13 +249,16 @@ struct lh_learn {
   char *arena = nullptr;
   double *hist[3] = {nullptr, nullptr, nullptr};
   int count = 0, head = 0;   // solutions stored, next ring slot
-  float *X = nullptr, *Y = nullptr, *evB = nullptr, *evA32 = nullptr;
+  float *X = nullptr, *Y = nullptr, *evA32 = nullptr;
+  double *bprev = nullptr;   // right-hand side of the previous solve
+  int stride = 1;            // recording: every stride-th element of a solve
   float *mq32 = nullptr;     // FP32 mass data for the residual check (own copy for FP64 contexts)
   double *guess = nullptr, *scale = nullptr, *part = nullptr, *ratio = nullptr;
   int *flag = nullptr, *used = nullptr;
   float *dX = nullptr, *dT = nullptr;
   int capacity = 0, rows = 0, solves = 0, predicted = 0;
   bool pending = false;      // features of the current solve were recorded
+  int pend_rows = 0, pend_off = 0;
   size_t smem_resid = 0;
   learn::Cent cent{};
   double hs = 1.0;
@@ -272,19 +282,25 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
   k_scale_final<<<1, 32, 0, s>>>(kBlocks, L->part, L->scale);
   float *X = L->X;
   L->pending = false;
+  int rows = m.ne, stride = 1, off = 0;
   if (L->mode == 1) {
-    if (L->rows + m.ne > L->capacity) return LH_OK;
+    stride = L->stride;
+    off = L->solves % stride;
+    rows = off < m.ne ? (m.ne - off + stride - 1) / stride : 0;
+    if (rows == 0 || L->rows + rows > L->capacity) return LH_OK;
     X = L->dX + (size_t)L->rows * kIn;
     L->pending = true;
+    L->pend_rows = rows;
+    L->pend_off = off;
   }
-  k_hist_features<<<4 * kBlocks, 256, 0, s>>>(m, a1, hist_at(L, 1), hist_at(L, 2), L->scale, X);
-  k_jac_features<<<(m.ne + 255) / 256, 256, 0, s>>>(m, x, L->cent, L->hs, X);
+  k_hist_features<<<4 * kBlocks, 256, 0, s>>>(m, rows, stride, off, a1, hist_at(L, 1), hist_at(L, 2), L->scale, X);
+  k_jac_features<<<(rows + 255) / 256, 256, 0, s>>>(m, rows, stride, off, x, L->cent, L->hs, X);
   if (L->mode == 2) {
     if (lh_status st = lh_mlp_forward(L->mlp, X, m.ne, L->Y, (lh_stream_t)s)) return st;
     k_assemble<<<2 * kBlocks, 256, 0, s>>>(m, L->Y, a1, L->scale, c->invdiag, L->guess);
-    k_resid_elem<<<c->grid_elem, F::THREADS, L->smem_resid, s>>>(
-        m, c->tab, L->mq32, L->guess, a1, c->invdiag, L->evA32, L->evB);
-    k_resid_nodes<<<kBlocks, 256, 0, s>>>(m, c->rhs, c->invdiag, L->evA32, L->evB, L->part);
+    k_resid_elem<<<c->grid_elem, F::THREADS, L->smem_resid, s>>>(m, c->tab, L->mq32, L->guess, c->invdiag,
+                                                                    L->evA32);
+    k_resid_nodes<<<kBlocks, 256, 0, s>>>(m, c->rhs, L->bprev, c->invdiag, L->evA32, L->part);
     k_decide<<<1, 32, 0, s>>>(kBlocks, L->part, L->flag, L->used, L->ratio);
     k_apply<<<kBlocks, 256, 0, s>>>(nv, L->flag, L->guess, c->a_prev);
     L->predicted += 1;
@@ -303,12 +319,13 @@ lh_status learn_after_solve(lh_ctx *c, cudaStream_t s) {
   if (!L || L->mode == 0) return LH_OK;
   using namespace learn;
   if (L->mode == 1 && L->pending) {
-    k_targets<<<4 * kBlocks, 256, 0, s>>>(c->mesh, c->a_prev, hist_at(L, 0), L->scale,
-                                          L->dT + (size_t)L->rows * kOut);
-    L->rows += c->mesh.ne;
+    k_targets<<<4 * kBlocks, 256, 0, s>>>(c->mesh, L->pend_rows, L->stride, L->pend_off, c->a_prev,
+                                          hist_at(L, 0), L->scale, L->dT + (size_t)L->rows * kOut);
+    L->rows += L->pend_rows;
     L->pending = false;
   }
   cudaMemcpyAsync(L->hist[L->head], c->a_prev, c->nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(L->bprev, c->rhs, c->nv * sizeof(double), cudaMemcpyDeviceToDevice, s);
   L->head = (L->head + 1) % 3;
   L->count = L->count < 3 ? L->count + 1 : 3;
   L->solves += 1;
@@ -362,7 +379,7 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   const bool own_mq32 = c->mq32 == nullptr;
   const size_t nq = ne * (size_t)c->nq;
   const size_t bytes_list[] = {3 * nv * 8, ne * lh::mlp::kIn * 4, ne * lh::mlp::kOut * 4, ne * 3 * 64 * 4,
-                               ne * 3 * 64 * 4, nv * 8, 4 * 1184 * 8 + 1024, own_mq32 ? nq * 4 : 0};
+                               nv * 8, nv * 8, 4 * 1184 * 8 + 1024, own_mq32 ? nq * 4 : 0};
   size_t bytes = 0;
   for (size_t b : bytes_list) bytes += (b + 255) / 256 * 256;
   if (cudaMalloc(&L->arena, bytes) != cudaSuccess) {
@@ -378,7 +395,7 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   L->X = (float *)take(bytes_list[1]);
   L->Y = (float *)take(bytes_list[2]);
   L->evA32 = (float *)take(bytes_list[3]);
-  L->evB = (float *)take(bytes_list[4]);
+  L->bprev = (double *)take(bytes_list[4]);
   L->guess = (double *)take(bytes_list[5]);
   char *misc = take(bytes_list[6]);
   L->mq32 = own_mq32 ? (float *)take(bytes_list[7]) : c->mq32;
@@ -396,6 +413,12 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   if (own_mq32) lh::learn::k_to_f32<<<1024, 256>>>(nq, c->mq, L->mq32);
   c->learn = L;
   return cudaDeviceSynchronize() == cudaSuccess ? LH_OK : LH_ERR_CUDA;
+}
+
+lh_status lh_learn_set_record_stride(lh_ctx *c, int stride) {
+  if (!c || !c->learn || stride < 1) return LH_ERR_ARG;
+  c->learn->stride = stride;
+  return LH_OK;
 }
 
 lh_status lh_learn_stats(const lh_ctx *c, int *rows_recorded, int *solves, int *predictions, int *learned_used,

@@ -30,7 +30,7 @@ EXPORTED = ["lh_setup", "lh_destroy", "lh_get_sizes", "lh_last_error", "lh_sync_
             "lh_batch_destroy",
             "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_get_params", "lh_mlp_set_params",
             "lh_mlp_forward", "lh_mlp_gradients", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_sync_status",
-            "lh_learn_attach",
+            "lh_learn_attach", "lh_learn_set_record_stride",
             "lh_learn_stats", "lh_selftest_barrier_timeout", "lh_timing_enable", "lh_timing_read", "lh_mass_mult_tc",
             "lh_remap_velocity", "lh_remap_apply", "lh_stiffness_setup", "lh_stiffness_mult", "lh_laplacian",
             "lh_tmop_objective", "lh_tmop_gradient", "lh_tmop_hessian_mult", "lh_tmop_hessian_diag",
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "lh_mlp_last_error": (ctypes.c_char_p, [P]),
         "lh_mlp_sync_status": (I, [P]),
         "lh_learn_attach": (I, [P, P, I, VP, VP, I]),
+        "lh_learn_set_record_stride": (I, [P, I]),
         "lh_selftest_barrier_timeout": (I, [ctypes.POINTER(I)]),
         "lh_timing_enable": (I, [P, I]),
         "lh_set_dt_control": (I, [P, I]),
@@ -516,6 +517,11 @@ def learn_attach(ctx, mlp, mode, X_buf=None, T_buf=None):
     cap = 0 if X_buf is None else int(X_buf.shape[0])
     ctx._check(ctx.lib.lh_learn_attach(ctx.h, mlp.h if mlp is not None else None, int(mode), _ptr(X_buf),
                                        _ptr(T_buf), cap))
+
+
+def learn_set_record_stride(ctx, stride):
+    """Recording keeps every stride-th element of each solve (rotating subset)."""
+    ctx._check(ctx.lib.lh_learn_set_record_stride(ctx.h, int(stride)))
 
 
 def learn_stats(ctx):

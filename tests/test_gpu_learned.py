@@ -107,3 +107,56 @@ def test_learned_guess_keeps_the_solution_and_is_used():
     for a, b in zip(states["learned"], (xo, vo, eo)):
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
     net.close()
+
+
+def test_trained_guess_on_held_out_seed_reports_gain_or_loss(record_property):
+    """The network trained on the configured budget (weights committed beside the
+    package) on held-out seed 9 of the learned workload (48^3 Q3/Q2, jitter 0.1h), FP32
+    inner solver: the same run with and without the learned guess. The guess must win
+    the residual comparison, must not cost CG iterations, and must leave the state
+    unchanged within the precision form's bar; the measured time ratio and iteration
+    saving are reported (record_property and stdout), a loss included."""
+    import os
+
+    from paper_2112_07075_b300.learned import LEARNED_N, load_weights
+    from paper_2112_07075_b300.lh import Context, learn_attach, learn_stats
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2112_07075_b300", "weights", "mlp_tg3d48_q3.npz")
+    assert os.path.exists(path), "trained weights missing"
+    net = load_weights(path)
+    V = inputs.box_vertices(3, LEARNED_N, jitter=0.1, seed=9)
+    stream = torch.cuda.current_stream()
+    runs = {}
+    for mode in ("plain", "learned"):
+        c = Context(3, LEARNED_N, V, 3, 6, precision="fp32_ir")
+        if mode == "learned":
+            learn_attach(c, net, 2)
+        x, v, e = c.init_state()
+        info = c.new_step_info(0.0, 1.0)
+        ms, its = [], []
+        for k in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.rk2avg_step(x, v, e, 0.0, info)
+            b.record(stream)
+            b.synchronize()
+            if k >= 2:
+                ms.append(a.elapsed_time(b))
+                its.append(sum(c.read_step_info(info).cg_iters))
+        assert c.sync_status() == 0
+        st = learn_stats(c) if mode == "learned" else None
+        runs[mode] = (np.mean(ms), np.mean(its), [t.cpu().numpy() for t in (x, v, e)], st)
+        c.close()
+    net.close()
+    (tp, ip, sp, _), (tl, il, sl, st) = runs["plain"], runs["learned"]
+    gain, saved = tp / tl, ip - il
+    record_property("time_ratio_plain_over_learned", gain)
+    record_property("cg_iters_saved_per_step", saved)
+    print(f"learned guess: {gain:.3f}x step time ({tp:.2f} vs {tl:.2f} ms), {saved:+.2f} CG iterations per step "
+          f"({ip:.2f} vs {il:.2f}), used in {st['used']} of {st['predictions']} solves, residual ratio "
+          f"{st['mean_residual_ratio']:.3f}")
+    assert st["predictions"] > 0 and st["used"] > 0
+    assert st["mean_residual_ratio"] < 1.0
+    assert il <= ip + 0.5
+    for a_, b_ in zip(sl, sp):
+        assert np.linalg.norm(a_ - b_) <= 1e-10 * np.linalg.norm(b_)
