@@ -39,6 +39,7 @@ struct ItemN {      // node work item: scalar H1 nodes [g0, g1) of problem pid
 struct BProb {      // per-problem record used by node kernels and the batched solver
   MeshDesc m;
   int order, n_nitems, first_nitem, source;
+  int n_eitems, first_eitem;             // the problem's solver element items (set with the tiles)
   const double *tab, *mq, *invdiag, *dt;
   const int *ncopy;                      // the problem's node-copy table [N_H1][4]
   double *evec, *r, *p, *ap, *a, *rhs;   // a = acceleration (CG solution, warm start)
@@ -175,6 +176,7 @@ struct BCgArgs {
   const ItemN *items_n;
   int nitems_n, nprob;
   double *partials;       // [nitems_n][3]
+  double *partials_e;     // [nitems_e]: per solver element item
   int *active;            // number of problems still iterating
   GridBarrier *bar;       // this launch's barrier (zero at launch)
   GridBarrier *bar_next;  // the next launch's barrier, zeroed at the end of this one
@@ -185,7 +187,10 @@ struct BCgArgs {
 };
 
 template <int P>
-__device__ __forceinline__ void b_cg_matvec(const BProb &pb, int e0, int mode, double beta, double *sm) {
+// E-vector of M u for one batch of the problem's elements (mode 0: u = a masked to
+// the free DOFs; mode 1: u = p_new = D^-1 r + beta p); returns this thread's share of
+// u . M u summed element by element (the search direction's energy p_new^T M p_new).
+__device__ __forceinline__ double b_cg_matvec(const BProb &pb, int e0, int mode, double beta, double *sm) {
   using F = F2<P>;
   constexpr int ND = F::ND, NQ = F::NQ, CXC = F::CXC;
   double *st = sm, *u = st + F::TAB, *S = u + CXC * ND, *uq = S + F::MC_S, *y = uq + CXC * NQ;
@@ -207,8 +212,14 @@ __device__ __forceinline__ void b_cg_matvec(const BProb &pb, int e0, int mode, d
   }
   __syncthreads();
   F::template batch_matvec<double>(st + F::oB, st + F::oBt, u, S, uq, y, pb.mq, e0, nb);
-  for (int k = threadIdx.x; k < nb * 2 * ND; k += blockDim.x) pb.evec[(size_t)e0 * 2 * ND + k] = y[k];
+  double d = 0.0;
+  for (int k = threadIdx.x; k < nb * 2 * ND; k += blockDim.x) {
+    const double yk = y[k];
+    pb.evec[(size_t)e0 * 2 * ND + k] = yk;
+    d = fma(u[k], yk, d);
+  }
   __syncthreads();
+  return d;
 }
 
 // Deterministic per-problem reduction of node-item partials: the last item of
@@ -237,6 +248,11 @@ __device__ __forceinline__ void sum_item_partials(const double *partials, int fi
   __syncthreads();
 }
 
+// One stage's solver launch: right-hand sides, then per problem the standard
+// Jacobi-PCG recurrences with two grid barriers per iteration (p_new^T M p_new is
+// summed element by element in the element sweep, so alpha is known after the first
+// barrier and one node sweep updates p, a, r and forms r.r, r.z), then the stage's
+// node update.
 __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
   extern __shared__ double sm[];
   __shared__ double red[32 * 3];
@@ -320,26 +336,46 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
   for (int iter = 0;; ++iter) {
     const int nact = *(volatile int *)A.active;
     if (nact == 0 || iter >= A.max_it) break;
-    // E: element matvec of p_new = invdiag r + beta p for active problems
+    // E: element matvec of p_new = invdiag r + beta p for active problems, with
+    // p_new . M p_new summed element by element; the last item of a problem sums the
+    // item partials in item order and forms alpha
     for (int it = blockIdx.x; it < A.nitems_e; it += G) {
       const ItemE w = A.items_e[it];
-      const BScal &sc = A.scal[w.pid];
+      BScal &sc = A.scal[w.pid];
       if (!sc.active) continue;
       const BProb &pb = A.probs[w.pid];
       const double beta = sc.beta;
+      double acc[1] = {0.0};
       dispatch_order(w.order, [&](auto P) {
         for (int b = 0; b < w.nbat; ++b)
-          b_cg_matvec<decltype(P)::value>(pb, w.e0 + b * F2<decltype(P)::value>::NBC, 1, beta, sm);
+          acc[0] += b_cg_matvec<decltype(P)::value>(pb, w.e0 + b * F2<decltype(P)::value>::NBC, 1, beta, sm);
       });
+      block_sum<1>(acc, red);
+      if (threadIdx.x == 0) A.partials_e[it] = acc[0];
+      if (last_item(sc, pb.n_eitems)) {
+        if (threadIdx.x < 32) {
+          __threadfence();
+          double t = 0.0;
+          for (int i = threadIdx.x; i < pb.n_eitems; i += 32)
+            t += ((volatile const double *)A.partials_e)[pb.first_eitem + i];
+          t = warp_sum(t);
+          if (threadIdx.x == 0) {
+            sc.cnt = 0;
+            sc.alpha = sc.rz / t;
+          }
+        }
+        __syncthreads();
+      }
     }
     if (!sync()) return;
-    // B: q = M p_new, p = p_new, p.q; alpha per problem
+    // B: one node sweep: q = M p_new gathered, p = p_new, a += alpha p, r -= alpha q,
+    // r.r and r.z; the last item of a problem forms beta and tests convergence
     for (int it = blockIdx.x; it < A.nitems_n; it += G) {
       const ItemN w = A.items_n[it];
       BScal &sc = A.scal[w.pid];
       if (!sc.active) continue;
       const BProb &pb = A.probs[w.pid];
-      const double beta = sc.beta;
+      const double alpha = sc.alpha, beta = sc.beta;
       double acc[3] = {0.0, 0.0, 0.0};
       const int g = w.g0 + threadIdx.x;
       if (g < w.g1) {
@@ -350,50 +386,20 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
           for (int c = 0; c < 2; ++c) {
             const int k = c * pb.m.nh1 + g;
             const double idg = pb.invdiag[k];
-            double qv = 0.0, pn = 0.0;
             if (idg != 0.0) {
-              qv = pb.evec[off[0] + c * ND];
+              double qv = pb.evec[off[0] + c * ND];
               for (int j = 1; j < n; ++j) qv += pb.evec[off[j] + c * ND];
-              pn = fma(beta, pb.p[k], idg * pb.r[k]);
-              acc[0] = fma(pn, qv, acc[0]);
+              const double rv = pb.r[k];
+              const double pn = fma(beta, pb.p[k], idg * rv);
+              const double r2 = fma(-alpha, qv, rv);
+              pb.p[k] = pn;
+              pb.a[k] = fma(alpha, pn, pb.a[k]);
+              pb.r[k] = r2;
+              acc[0] = fma(r2, r2, acc[0]);
+              acc[1] = fma(r2 * idg, r2, acc[1]);
             }
-            pb.ap[k] = qv;
-            pb.p[k] = pn;
           }
         });
-      }
-      block_sum<3>(acc, red);
-      if (threadIdx.x == 0) A.partials[(size_t)it * 3] = acc[0];
-      if (last_item(sc, pb.n_nitems)) {
-        sum_item_partials(A.partials, pb.first_nitem, pb.n_nitems, 1, s_v);
-        if (threadIdx.x == 0) {
-          sc.cnt = 0;
-          sc.alpha = sc.rz / s_v[0];
-        }
-      }
-    }
-    if (!sync()) return;
-    // C: a += alpha p, r -= alpha q, r.r, r.z; convergence and beta per problem
-    for (int it = blockIdx.x; it < A.nitems_n; it += G) {
-      const ItemN w = A.items_n[it];
-      BScal &sc = A.scal[w.pid];
-      if (!sc.active) continue;
-      const BProb &pb = A.probs[w.pid];
-      const double alpha = sc.alpha;
-      double acc[3] = {0.0, 0.0, 0.0};
-      const int g = w.g0 + threadIdx.x;
-      if (g < w.g1) {
-        for (int c = 0; c < 2; ++c) {
-          const int k = c * pb.m.nh1 + g;
-          const double idg = pb.invdiag[k];
-          if (idg != 0.0) {
-            pb.a[k] = fma(alpha, pb.p[k], pb.a[k]);
-            const double rv = fma(-alpha, pb.ap[k], pb.r[k]);
-            pb.r[k] = rv;
-            acc[0] = fma(rv, rv, acc[0]);
-            acc[1] = fma(rv * idg, rv, acc[1]);
-          }
-        }
       }
       block_sum<3>(acc, red);
       if (threadIdx.x == 0) {
@@ -471,7 +477,8 @@ struct lh_batch {
   ItemE *items_e = nullptr, *items_cg = nullptr;
   ItemN *items_n = nullptr;
   int n_items_e = 0, n_items_cg = 0, n_items_n = 0, cap_items_e = 0, cap_items_cg = 0;
-  double *partials = nullptr, *dts = nullptr;
+  double *partials = nullptr, *partials_e = nullptr, *dts = nullptr;
+  std::vector<BProb> probs_host;   // host copy: the solver item ranges change with the tiles
   int *active = nullptr, *status = nullptr;
   GridBarrier *bar = nullptr;   // two: one per stage's solver launch
   int grid_e[3] = {0, 0, 0};    // per element block size 128, 256, 512
@@ -529,6 +536,17 @@ static std::vector<ItemE> make_items(const lh_batch *b, const int *tiles, NBF nb
   return items;
 }
 
+// Each problem's solver element items are contiguous in the work list (sorted by
+// order, then problem): record where they start and how many there are.
+static void set_solver_ranges(std::vector<BProb> &pr, const std::vector<ItemE> &ic) {
+  for (auto &p : pr) { p.first_eitem = 0; p.n_eitems = 0; }
+  for (int k = 0; k < (int)ic.size(); ++k) {
+    BProb &p = pr[ic[k].pid];
+    if (p.n_eitems == 0) p.first_eitem = k;
+    p.n_eitems += 1;
+  }
+}
+
 static lh_status upload_items(lh_batch *b) {
   std::vector<ItemE> ie = make_items(b, b->tiles, nb_of);
   std::vector<ItemE> ic = make_items(b, b->tiles_cg, nbc_of);
@@ -538,6 +556,8 @@ static lh_status upload_items(lh_batch *b) {
   BCUDA(b, cudaMemcpy(b->items_cg, ic.data(), ic.size() * sizeof(ItemE), cudaMemcpyHostToDevice));
   b->n_items_e = (int)ie.size();
   b->n_items_cg = (int)ic.size();
+  set_solver_ranges(b->probs_host, ic);
+  BCUDA(b, cudaMemcpy(b->probs, b->probs_host.data(), b->probs_host.size() * sizeof(BProb), cudaMemcpyHostToDevice));
   return LH_OK;
 }
 
@@ -625,7 +645,8 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
       {(void **)&b->t2, n * sizeof(ForceTArgs)},  {(void **)&b->probs, n * sizeof(BProb)},
       {(void **)&b->scal, n * sizeof(BScal)},     {(void **)&b->items_e, nie * sizeof(ItemE)},
       {(void **)&b->items_cg, nic * sizeof(ItemE)}, {(void **)&b->items_n, nin * sizeof(ItemN)},
-      {(void **)&b->partials, nin * 3 * sizeof(double)}, {(void **)&b->dts, n * sizeof(double)},
+      {(void **)&b->partials, nin * 3 * sizeof(double)}, {(void **)&b->partials_e, nic * sizeof(double)},
+      {(void **)&b->dts, n * sizeof(double)},
       {(void **)&b->active, 64}, {(void **)&b->status, 64}, {(void **)&b->bar, 2 * sizeof(GridBarrier)}};
   size_t bytes = 0;
   for (auto &it : items) bytes += (it.bytes + 255) / 256 * 256;
@@ -642,6 +663,8 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
   }
   cudaMemset(b->arena, 0, bytes);
   for (int i = 0; i < n; ++i) pr[i].dt = b->dts + i;
+  set_solver_ranges(pr, ic);
+  b->probs_host = pr;
   // per-problem argument structs
   std::vector<QdataArgs> q1(n), q2(n);
   std::vector<ForceArgs> fa(n);
@@ -754,7 +777,8 @@ static lh_status enqueue_step(lh_batch *b, double tol, int max_it, cudaStream_t 
   };
   auto cg = [&](int stage) -> lh_status {
     BCgArgs a{b->probs, b->scal, b->items_cg, b->n_items_cg, b->items_n, b->n_items_n, b->n,
-              b->partials, b->active, b->bar + stage, b->bar + (1 - stage), b->status, stage, tol, max_it};
+              b->partials, b->partials_e, b->active, b->bar + stage, b->bar + (1 - stage), b->status, stage,
+              tol, max_it};
     void *args[] = {&a};
     BCUDA(b, cudaLaunchCooperativeKernel((const void *)k_b_cg, dim3(b->grid_cg), dim3(kThreadsCG), args,
                                          b->smem_cg, s));

@@ -222,9 +222,53 @@ __device__ __forceinline__ double eig_min2(double a, double b, double c, double 
   return lam;
 }
 
-// Smallest eigenvalue of a symmetric 3x3 (A[0..8], row-major, symmetric) by the
-// trigonometric closed form (Smith 1961) and, if s != nullptr, its unit eigenvector
-// from the largest cross product of two rows of (A - lam I).
+// Smallest root mu of the characteristic polynomial of the trace-free symmetric
+// B = A - qI (diagonal d0, d1, d2; off-diagonal a01, a02, a12; p2 = tr B^2):
+// f(mu) = det(B - mu I) = -mu^3 + (p2 / 2) mu + det B. B is first scaled by a power
+// of two s with s^2 p2 in [1, 4) (exact), so the FP32 parts below neither underflow
+// nor overflow whatever the magnitude of A. Seed: the trigonometric closed form
+// evaluated in FP32 (cheap on B300, where FP64 runs at 1/64 of the FP32 rate);
+// then two Newton steps t -= f(t) / f'(t) in FP64 on the scaled polynomial (Newton's
+// method for a simple polynomial root; the step uses an FP32 reciprocal of f', which
+// changes only the quadratic convergence constant: each step still squares the
+// relative error down to rounding). Returns false when the root is not well
+// separated, |f'(t0)| < 0.05 tr (sB)^2 (a double or triple smallest eigenvalue), or
+// p2 is zero, subnormal or not finite: f is then flat near the root (or there is
+// nothing to refine) and the caller takes the FP64 trigonometric form. Where it
+// returns true the root is accurate to a few units of rounding of sqrt(p2).
+__device__ __forceinline__ bool eig_min3_newton(double d0, double d1, double d2, double a01, double a02, double a12,
+                                                double p2, double &mu) {
+  if (!(p2 > 1e-300) || !(p2 < 1e300)) return false;
+  const int ex = ((__double2hiint(p2) >> 20) & 0x7ff) - 1023;   // p2 = m 2^ex, m in [1, 2)
+  const int h = ex >> 1;                                        // floor(ex / 2)
+  const double sc = __hiloint2double((1023 - h) << 20, 0);      // 2^-h
+  const double e0 = d0 * sc, e1 = d1 * sc, e2 = d2 * sc, e01 = a01 * sc, e02 = a02 * sc, e12 = a12 * sc;
+  const double q2 = p2 * sc * sc;                               // tr (sB)^2 in [1, 4)
+  const float ppf = sqrtf((float)q2 * (1.0f / 6.0f)), ipf = 1.0f / ppf;
+  const float b00 = (float)e0 * ipf, b11 = (float)e1 * ipf, b22 = (float)e2 * ipf;
+  const float b01 = (float)e01 * ipf, b02 = (float)e02 * ipf, b12 = (float)e12 * ipf;
+  const float detbf = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+  const float rf = fminf(fmaxf(0.5f * detbf, -1.0f), 1.0f);
+  double t = (double)(2.0f * ppf * __cosf(acosf(rf) * (1.0f / 3.0f) + 2.0943951f));
+  const double c1 = 0.5 * q2;
+  double fp = fma(-3.0 * t, t, c1);
+  if (!(fabs(fp) >= 0.05 * q2)) return false;
+  const double detB = e0 * (e1 * e2 - e12 * e12) - e01 * (e01 * e2 - e12 * e02) + e02 * (e01 * e12 - e1 * e02);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double f = fma(fma(-t, t, c1), t, detB);
+    fp = fma(-3.0 * t, t, c1);
+    t = fma(-f, (double)(1.0f / (float)fp), t);
+  }
+  mu = t * __hiloint2double((1023 + h) << 20, 0);               // t / s
+  return true;
+}
+
+// Smallest eigenvalue of a symmetric 3x3 (A[0..8], row-major, symmetric) and, if
+// s != nullptr, its unit eigenvector from the largest cross product of two rows of
+// (A - lam I). The eigenvalue: Newton-polished root of the characteristic cubic
+// (eig_min3_newton) where it is well separated, else the FP64 trigonometric closed
+// form (Smith 1961).
 __device__ __forceinline__ double eig_min3(const double *A, double *s) {
   const double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[4], a12 = A[5], a22 = A[8];
   constexpr double third = 1.0 / 3.0, sixth = 1.0 / 6.0;
@@ -232,15 +276,20 @@ __device__ __forceinline__ double eig_min3(const double *A, double *s) {
   const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
   const double d0 = a00 - q, d1 = a11 - q, d2 = a22 - q;
   const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
-  const double pp = sqrt(p2 * sixth);
-  double lam = q;
-  if (pp > 0.0) {
-    const double ip = 1.0 / pp;
-    const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
-    const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
-    const double r = fmin(fmax(0.5 * detb, -1.0), 1.0);
-    const double phi = acos(r) * third;
-    lam = q + 2.0 * pp * cos(phi + 2.0943951023931957);  // 2*pi/3
+  double lam = q, mu;
+  if (eig_min3_newton(d0, d1, d2, a01, a02, a12, p2, mu)) {
+    lam = q + mu;
+  } else {
+    const double pp = sqrt(p2 * sixth);
+    if (pp > 0.0) {
+      const double ip = 1.0 / pp;
+      const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip, b01 = a01 * ip, b02 = a02 * ip, b12 = a12 * ip;
+      const double detb =
+          b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+      const double r = fmin(fmax(0.5 * detb, -1.0), 1.0);
+      const double phi = acos(r) * third;
+      lam = q + 2.0 * pp * cos(phi + 2.0943951023931957);  // 2*pi/3
+    }
   }
   if (s) {
     const double m00 = a00 - lam, m11 = a11 - lam, m22 = a22 - lam;
