@@ -431,7 +431,7 @@ lh_status lh_batch_create(int n, lh_ctx *const *ctxs, double *const *x, double *
  * 256 or 512; every per-value result is the same for any choice).
  *
  * lh_batch_autotune times whole batched steps (element passes and solver) for
- * candidate shapes -- per order element tiles 1, 2, 4 and solver tiles 1, 2, then
+ * candidate shapes -- per order element tiles 1, 2, 4 and solver tiles 1, 2, 4, then
  * 128, 256, 512 threads per block -- and keeps each change that makes the step at
  * least 1 % faster. Every trial starts from the same state and the problems'
  * states, warm starts and step records are restored at the end, so tuning leaves

@@ -55,7 +55,7 @@ struct BScal {      // per-problem CG scalars (device)
 
 constexpr int kThreads = 256;        // element kernels of all 2D families
 constexpr int kThreadsCG = 512;      // batched solver CTAs
-constexpr int kNodeItem = 512;       // nodes per node work item (one per solver thread)
+constexpr int kNodeItem = 2048;      // nodes per node work item (four per solver thread)
 
 static_assert(F2<1>::THREADS == kThreads && F2<2>::THREADS == kThreads && F2<3>::THREADS == kThreads &&
                   F2<4>::THREADS == kThreads, "2D families must share the element block size");
@@ -117,40 +117,39 @@ __device__ __forceinline__ int table_copies(const int *__restrict__ tab, int g, 
 // ---- node phases of the batched solver launch (one thread per scalar node) --
 // rhs = -(F.1) gathered from the E-vector, zero on constrained DOFs.
 __device__ __forceinline__ void node_rhs(const BProb &pb, const ItemN &w) {
-  const int g = w.g0 + threadIdx.x;
-  if (g >= w.g1) return;
   dispatch_order(pb.order, [&](auto P) {
     constexpr int D = decltype(P)::value + 1, ND = D * D;
-    int off[4];
-    const int n = table_copies(pb.ncopy, g, off);
-    for (int c = 0; c < 2; ++c) {
-      const int k = c * pb.m.nh1 + g;
-      double s = pb.evec[off[0] + c * ND];
-      for (int j = 1; j < n; ++j) s += pb.evec[off[j] + c * ND];
-      pb.rhs[k] = pb.invdiag[k] != 0.0 ? -s : 0.0;
+    for (int g = w.g0 + threadIdx.x; g < w.g1; g += blockDim.x) {
+      int off[4];
+      const int n = table_copies(pb.ncopy, g, off);
+      for (int c = 0; c < 2; ++c) {
+        const int k = c * pb.m.nh1 + g;
+        double s = pb.evec[off[0] + c * ND];
+        for (int j = 1; j < n; ++j) s += pb.evec[off[j] + c * ND];
+        pb.rhs[k] = pb.invdiag[k] != 0.0 ? -s : 0.0;
+      }
     }
   });
 }
 
 // Stage-1 update: vb0 = v + dt/2 a0, v_h = vb0, x_h = x + dt/2 vb0.
 __device__ __forceinline__ void node_mid(const BProb &pb, const ItemN &w) {
-  const int g = w.g0 + threadIdx.x;
-  if (g >= w.g1) return;
   const double hdt = 0.5 * *pb.dt;
-  for (int c = 0; c < 2; ++c) {
-    const int k = c * pb.m.nh1 + g;
-    const double vb = fma(hdt, pb.a[k], pb.v[k]);
-    pb.vh[k] = vb;
-    pb.xh[k] = fma(hdt, vb, pb.x[k]);
+  for (int g = w.g0 + threadIdx.x; g < w.g1; g += blockDim.x) {
+    for (int c = 0; c < 2; ++c) {
+      const int k = c * pb.m.nh1 + g;
+      const double vb = fma(hdt, pb.a[k], pb.v[k]);
+      pb.vh[k] = vb;
+      pb.xh[k] = fma(hdt, vb, pb.x[k]);
+    }
   }
 }
 
 // Final update: vb = v + dt/2 a, x += dt vb, v += dt a; node item 0 of a problem
 // also advances its step record.
 __device__ __forceinline__ void node_final(const BProb &pb, const ItemN &w) {
-  const int g = w.g0 + threadIdx.x;
   const double dt = *pb.dt, hdt = 0.5 * dt;
-  if (g < w.g1) {
+  for (int g = w.g0 + threadIdx.x; g < w.g1; g += blockDim.x) {
     for (int c = 0; c < 2; ++c) {
       const int k = c * pb.m.nh1 + g;
       const double ak = pb.a[k], vk = pb.v[k];
@@ -284,10 +283,9 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
     const ItemN w = A.items_n[it];
     const BProb &pb = A.probs[w.pid];
     double acc[3] = {0.0, 0.0, 0.0};
-    const int g = w.g0 + threadIdx.x;
-    if (g < w.g1) {
-      dispatch_order(pb.order, [&](auto P) {
-        constexpr int D = decltype(P)::value + 1, ND = D * D;
+    dispatch_order(pb.order, [&](auto P) {
+      constexpr int D = decltype(P)::value + 1, ND = D * D;
+      for (int g = w.g0 + threadIdx.x; g < w.g1; g += blockDim.x) {
         int off[4];
         const int n = table_copies(pb.ncopy, g, off);
         for (int c = 0; c < 2; ++c) {
@@ -309,8 +307,8 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
           pb.p[k] = 0.0;
           pb.ap[k] = 0.0;
         }
-      });
-    }
+      }
+    });
     block_sum<3>(acc, red);
     if (threadIdx.x == 0)
       for (int q = 0; q < 3; ++q) A.partials[(size_t)it * 3 + q] = acc[q];
@@ -377,10 +375,9 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
       const BProb &pb = A.probs[w.pid];
       const double alpha = sc.alpha, beta = sc.beta;
       double acc[3] = {0.0, 0.0, 0.0};
-      const int g = w.g0 + threadIdx.x;
-      if (g < w.g1) {
-        dispatch_order(pb.order, [&](auto P) {
-          constexpr int D = decltype(P)::value + 1, ND = D * D;
+      dispatch_order(pb.order, [&](auto P) {
+        constexpr int D = decltype(P)::value + 1, ND = D * D;
+        for (int g = w.g0 + threadIdx.x; g < w.g1; g += blockDim.x) {
           int off[4];
           const int n = table_copies(pb.ncopy, g, off);
           for (int c = 0; c < 2; ++c) {
@@ -399,8 +396,8 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
               acc[1] = fma(r2 * idg, r2, acc[1]);
             }
           }
-        });
-      }
+        }
+      });
       block_sum<3>(acc, red);
       if (threadIdx.x == 0) {
         A.partials[(size_t)it * 3] = acc[0];
@@ -849,7 +846,7 @@ lh_status lh_batch_set_config(lh_batch *b, const int *cfg) {
 // Autotuner: times whole batched steps (both element passes and the solver) for
 // candidate tile shapes and keeps, coordinate by coordinate, every change that
 // makes the step at least 1 % faster: per order the element tile (1, 2, 4
-// batches per work item) and the solver tile (1, 2), then the element passes'
+// batches per work item) and the solver tile (1, 2, 4), then the element passes'
 // threads per block (128, 256, 512). Every candidate starts from the same state
 // (x, v, e, the accelerations that warm-start the solves and the step records
 // are saved first and restored after each trial and at the end), so the
@@ -945,7 +942,8 @@ lh_status lh_batch_autotune(lh_batch *b, int *cfg_out) {
       if (!present) continue;
       for (int t : {2, 4})
         if ((result = try_cfg(p - 1, t)) != LH_OK) break;
-      if (result == LH_OK) result = try_cfg(3 + p, 2);
+      for (int t : {2, 4})
+        if (result == LH_OK) result = try_cfg(3 + p, t);
     }
     for (int t : {128, 512})
       if (result == LH_OK) result = try_cfg(8, t);

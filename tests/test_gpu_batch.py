@@ -79,8 +79,11 @@ def test_batched_steps_match_unbatched_and_oracle():
 def test_configured_256_problem_batch_matches_one_by_one_and_oracle():
     """The batching workload as configured: 256 problems from generator seed 4 (orders 1-4,
     n in [8, 64], half Taylor-Green, half Gresho), fixed dt_k = 0.5 dt_est_k(S0), 20 steps.
-    Every problem against its own lh_rk2avg_step run (1e-12 per field); the smallest
-    problem of each (order, kind) against the oracle (1e-11 per field)."""
+    Every problem against its own lh_rk2avg_step run and the smallest problem of each
+    (order, kind) against the oracle, 1e-11 per field: the batched solver sums its dot
+    products in another order, so its solves differ from the one-by-one ones within the
+    CG tolerance (1e-12 relative residual), which after 20 steps is the 1e-11 budget of
+    the parity tests."""
     from paper_2112_07075_b300.lh import Batch, Context
     probs = inputs.batch_problems(4)
     steps = 20
@@ -117,7 +120,7 @@ def test_configured_256_problem_batch_matches_one_by_one_and_oracle():
             a = a.cpu().numpy()
             err = np.linalg.norm(a - b) / np.linalg.norm(b)
             worst = max(worst, err)
-            assert err <= 1e-12, (i, probs[i], err)
+            assert err <= 1e-11, (i, probs[i], err)
     # oracle: the smallest problem of every (order, kind)
     picks = {}
     for i, pr in enumerate(probs):
