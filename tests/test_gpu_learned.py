@@ -160,3 +160,37 @@ def test_trained_guess_on_held_out_seed_reports_gain_or_loss(record_property):
     assert il <= ip + 0.5
     for a_, b_ in zip(sl, sp):
         assert np.linalg.norm(a_ - b_) <= 1e-10 * np.linalg.norm(b_)
+
+
+def test_trained_guess_reduced_workload_matches_oracle():
+    """The learned workload's element family and mesh statistics on a 6^3 mesh (Q3/Q2,
+    q1 = 6, jitter 0.1h, held-out seed 9), 20 CFL steps with the FP32 inner solver and
+    the trained guess, against the oracle: every field within the precision form's
+    1e-10."""
+    import os
+
+    from paper_2112_07075_b300.learned import load_weights
+    from paper_2112_07075_b300.lh import Context, learn_attach, learn_stats
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2112_07075_b300", "weights", "mlp_tg3d48_q3.npz")
+    net = load_weights(path, max_rows=8192)
+    V = inputs.box_vertices(3, 6, jitter=0.1, seed=9)
+    c = Context(3, 6, V, 3, 6, precision="fp32_ir")
+    learn_attach(c, net, 2)
+    x, v, e = c.init_state()
+    info = c.new_step_info(0.0, 1.0)
+    for _ in range(20):
+        c.rk2avg_step(x, v, e, 0.0, info)
+    st = learn_stats(c)
+    assert c.sync_status() == 0 and st["predictions"] > 0
+    gpu = [t.cpu().numpy().reshape(-1) for t in (x, v, e)]
+    c.close()
+    net.close()
+    hy = Hydro(Params(dim=3, n=6, order=3, q1=6, vertices=V))
+    xo, vo, eo = hy.initial_state("taylor_green")
+    t = 0.0
+    for _ in range(20):
+        xo, vo, eo, oi = hy.rk2avg_step(xo, vo, eo, dt=None, t=t, t_end=1.0)
+        t += oi.dt
+    for a, b in zip(gpu, (xo.reshape(-1), vo.reshape(-1), eo.reshape(-1))):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
