@@ -125,13 +125,43 @@ def load_weights(path, max_rows=LEARNED_N ** 3):
     return net
 
 
+def evaluate(path, steps, precision="fp32_ir", seed=HELD_OUT_SEEDS[0], learned=True):
+    """CFL steps from t = 0 of the learned workload on a held-out seed with the weights
+    at `path` (learned=False: the plain previous-solve guess). Returns the step record."""
+    import torch
+    from . import inputs
+    net = load_weights(path) if learned else None
+    c = lh.Context(3, LEARNED_N, inputs.box_vertices(3, LEARNED_N, jitter=LEARNED_JITTER, seed=seed),
+                   LEARNED_ORDER, LEARNED_Q1, precision=precision)
+    if net is not None:
+        lh.learn_attach(c, net, 2)
+    x, v, e = c.init_state()
+    info = c.new_step_info(0.0, 1.0)
+    for _ in range(steps):
+        c.rk2avg_step(x, v, e, 0.0, info)
+    torch.cuda.synchronize()
+    si = c.read_step_info(info)
+    c.close()
+    if net is not None:
+        net.close()
+    return si
+
+
 if __name__ == "__main__":
     import argparse
     import json
-    ap = argparse.ArgumentParser(description="train the learned-form MLP on the configured budget")
-    ap.add_argument("--out", required=True)
+    ap = argparse.ArgumentParser(description="train the learned-form MLP on the configured budget, or "
+                                             "evaluate trained weights on a held-out seed")
+    ap.add_argument("--out", help="train: write the weights here")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--stride", type=int, default=32)
+    ap.add_argument("--eval", help="evaluate these weights instead of training")
+    ap.add_argument("--eval-steps", type=int, default=6)
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp64", "fp32_ir", "bf16tc_ir"])
     a = ap.parse_args()
-    rows, hist, rs, ts = train_configured(a.out, a.steps, a.stride)
-    print(json.dumps({"rows": rows, "loss": hist, "record_s": rs, "train_s": ts}))
+    if a.eval:
+        si = evaluate(a.eval, a.eval_steps, a.precision)
+        print(json.dumps({"steps": si.steps, "t": si.t, "status": si.status, "cg_iters_last": list(si.cg_iters)}))
+    else:
+        rows, hist, rs, ts = train_configured(a.out, a.steps, a.stride)
+        print(json.dumps({"rows": rows, "loss": hist, "record_s": rs, "train_s": ts}))
