@@ -80,21 +80,26 @@ __global__ void k_scale_final(int nb, const double *__restrict__ part, double *_
 // History features: X[e][c*64 + i] = a_1 / s, X[e][192 + c*64 + i] = (a_1 - a_2) / s_d,
 // X[e][384 + c*64 + i] = (a_2 - a_3) / s_d at node(e, i), component c.
 // Row r of X holds element e = off + r * stride (stride 1, off 0: every element).
+// One thread per (row, element node): the node's index is formed once and its three
+// components of the three history vectors give nine features.
 __global__ void k_hist_features(MeshDesc m, int rows, int stride, int off, const double *__restrict__ h0,
                                 const double *__restrict__ h1, const double *__restrict__ h2,
                                 const double *__restrict__ s, float *__restrict__ X) {
-  const size_t total = (size_t)rows * 576;
+  const size_t total = (size_t)rows * ND;
   const double is = 1.0 / s[0], isd = 1.0 / s[1];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / 576), f = (int)(t % 576);
+    const int r = (int)(t / ND), i = (int)(t % ND);
     const int e = off + r * stride;
-    const int k = f / 192, c = (f / 64) % 3, i = f % 64;
-    const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
-    double val;
-    if (k == 0) val = h0[gi] * is;
-    else if (k == 1) val = (h0[gi] - h1[gi]) * isd;
-    else val = (h1[gi] - h2[gi]) * isd;
-    X[(size_t)r * kIn + f] = (float)val;
+    const size_t g = (size_t)h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
+    float *xr = X + (size_t)r * kIn;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t gi = (size_t)c * m.nh1 + g;
+      const double a0 = h0[gi], a1 = h1[gi], a2 = h2[gi];
+      xr[c * ND + i] = (float)(a0 * is);
+      xr[192 + c * ND + i] = (float)((a0 - a1) * isd);
+      xr[384 + c * ND + i] = (float)((a1 - a2) * isd);
+    }
   }
 }
 
@@ -156,16 +161,21 @@ __global__ void k_assemble(MeshDesc m, const float *__restrict__ Y, const double
   }
 }
 
-// FP32 E-vector of M g for the residual comparison.
-__global__ void __launch_bounds__(F::THREADS) k_resid_elem(MeshDesc m, const double *__restrict__ tab,
-                                                           const float *__restrict__ mq32, const double *__restrict__ g,
-                                                           const double *__restrict__ idg, float *__restrict__ evA) {
-  constexpr int CX = F::CX, NQ = F::NQ, Q = 6;
-  constexpr int MS = F::M_S;
+// FP32 E-vector of M g for the residual comparison: kResidNb elements per CTA (one
+// element per CTA left most of each 224-thread block idle at 216 qpoints).
+constexpr int kResidNb = 8, kResidCx = 3 * kResidNb, kResidThreads = 256;
+constexpr int kResidS = interp_scratch<3, D, 6>(kResidCx) > interp_scratch<3, 6, D>(kResidCx)
+                            ? interp_scratch<3, D, 6>(kResidCx) : interp_scratch<3, 6, D>(kResidCx);
+constexpr size_t kResidSmem = sizeof(float) * (2 * 6 * D + kResidCx * ND + kResidS + kResidCx * 216 + kResidCx * ND);
+__global__ void __launch_bounds__(kResidThreads) k_resid_elem(MeshDesc m, const double *__restrict__ tab,
+                                                              const float *__restrict__ mq32,
+                                                              const double *__restrict__ g,
+                                                              const double *__restrict__ idg, float *__restrict__ evA) {
+  constexpr int CX = kResidCx, NQ = 216, Q = 6;
   extern __shared__ double smd[];
-  float *tb = (float *)smd, *tbt = tb + Q * D, *u = tbt + Q * D, *S = u + CX * ND, *uq = S + MS, *y = uq + CX * NQ;
+  float *tb = (float *)smd, *tbt = tb + Q * D, *u = tbt + Q * D, *S = u + CX * ND, *uq = S + kResidS, *y = uq + CX * NQ;
   for (int k = threadIdx.x; k < 2 * Q * D; k += blockDim.x) tb[k] = (float)tab[k < Q * D ? F::oB + k : F::oBt + k - Q * D];
-  const int e0 = blockIdx.x * F::NB, nb = min(F::NB, m.ne - e0);
+  const int e0 = blockIdx.x * kResidNb, nb = min(kResidNb, m.ne - e0);
   for (int k = threadIdx.x; k < CX * ND; k += blockDim.x) {
     const int i = k % ND, bc = k / ND, c = bc % 3, b = bc / 3;
     float val = 0.0f;
@@ -298,8 +308,9 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
   if (L->mode == 2) {
     if (lh_status st = lh_mlp_forward(L->mlp, X, m.ne, L->Y, (lh_stream_t)s)) return st;
     k_assemble<<<2 * kBlocks, 256, 0, s>>>(m, L->Y, a1, L->scale, c->invdiag, L->guess);
-    k_resid_elem<<<c->grid_elem, F::THREADS, L->smem_resid, s>>>(m, c->tab, L->mq32, L->guess, c->invdiag,
-                                                                    L->evA32);
+    k_resid_elem<<<(m.ne + kResidNb - 1) / kResidNb, kResidThreads, L->smem_resid, s>>>(m, c->tab, L->mq32,
+                                                                                         L->guess, c->invdiag,
+                                                                                         L->evA32);
     k_resid_nodes<<<kBlocks, 256, 0, s>>>(m, c->rhs, L->bprev, c->invdiag, L->evA32, L->part);
     k_decide<<<1, 32, 0, s>>>(kBlocks, L->part, L->flag, L->used, L->ratio);
     k_apply<<<kBlocks, 256, 0, s>>>(nv, L->flag, L->guess, c->a_prev);
@@ -406,8 +417,7 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   L->used = L->flag + 1;
   lh::h1_basis_at(3, 0.5, L->cent.v, L->cent.d);
   L->hs = c->h0 * c->p;
-  const size_t smem = sizeof(float) * (2 * 6 * 4 + lh::learn::F::CX * 64 + lh::learn::F::M_S +
-                                       lh::learn::F::CX * lh::learn::F::NQ + lh::learn::F::CX * 64) + 16;
+  const size_t smem = lh::learn::kResidSmem + 16;
   cudaFuncSetAttribute((const void *)lh::learn::k_resid_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   L->smem_resid = smem;
   if (own_mq32) lh::learn::k_to_f32<<<1024, 256>>>(nq, c->mq, L->mq32);
