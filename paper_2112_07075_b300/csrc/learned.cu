@@ -106,28 +106,42 @@ __global__ void k_hist_features(MeshDesc m, int rows, int stride, int off, const
 // Jacobian features at the element centroid: 9 entries of J / (h0 p) and det J / (h0 p)^3.
 __global__ void k_jac_features(MeshDesc m, int rows, int stride, int off, const double *__restrict__ x, Cent cb,
                                double hs, float *__restrict__ X) {
+  // FP32 arithmetic (the features feed a BF16 network); positions are taken relative
+  // to the element's first node, which leaves J unchanged (the basis derivatives sum
+  // to zero) and avoids cancellation between O(1) coordinates
+  float cv[D], cd[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    cv[k] = (float)cb.v[k];
+    cd[k] = (float)cb.d[k];
+  }
+  const float ihs = (float)(1.0 / hs);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
     const int e = off + r * stride;
     const int base = h1_base<3, D>(m, e);
-    double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double x0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x0[c] = x[(size_t)c * m.nh1 + base];
+    float J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = 0; i < ND; ++i) {
       const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
-      const double gx = cb.d[ix] * cb.v[iy] * cb.v[iz];
-      const double gy = cb.v[ix] * cb.d[iy] * cb.v[iz];
-      const double gz = cb.v[ix] * cb.v[iy] * cb.d[iz];
+      const float gx = cd[ix] * cv[iy] * cv[iz];
+      const float gy = cv[ix] * cd[iy] * cv[iz];
+      const float gz = cv[ix] * cv[iy] * cd[iz];
       const int g = base + h1_local<3, D>(m, i);
+#pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double xc = x[(size_t)c * m.nh1 + g];
-        J[c * 3 + 0] += xc * gx;
-        J[c * 3 + 1] += xc * gy;
-        J[c * 3 + 2] += xc * gz;
+        const float xc = (float)(x[(size_t)c * m.nh1 + g] - x0[c]) * ihs;
+        J[c * 3 + 0] = fmaf(xc, gx, J[c * 3 + 0]);
+        J[c * 3 + 1] = fmaf(xc, gy, J[c * 3 + 1]);
+        J[c * 3 + 2] = fmaf(xc, gz, J[c * 3 + 2]);
       }
     }
-    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
-                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    const float det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                      J[2] * (J[3] * J[7] - J[4] * J[6]);
     float *out = X + (size_t)r * kIn + 576;
-    for (int k = 0; k < 9; ++k) out[k] = (float)(J[k] / hs);
-    out[9] = (float)(det / (hs * hs * hs));
+    for (int k = 0; k < 9; ++k) out[k] = J[k];
+    out[9] = det;
   }
 }
 
