@@ -92,8 +92,6 @@ def _energy(hy, v, e):
     return hy.kinetic_energy(v.reshape(3, -1)) + hy.internal_energy(e)
 
 
-@pytest.mark.skipif(not os.path.exists(G_SPREAD), reason="oracle spread file not written yet "
-                    "(tests/golden/make_tg3d24_spread.py)")
 def test_config2_whole_run_with_viscosity_within_oracle_spread(record_property):
     from oracle.hydro import Hydro, Params
     g = np.load(G_END)
