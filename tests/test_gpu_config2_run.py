@@ -112,4 +112,4 @@ def test_config2_whole_run_with_viscosity_within_oracle_spread(record_property):
     E0, E1 = _energy(hy, v0, e0), _energy(hy, state[1], state[2])
     record_property("energy_drift", (E1 - E0) / E0)
     print("total energy drift over the run", (E1 - E0) / E0)
-    assert abs(E1 - E0) <= 1e-9 * abs(E0)
+    assert abs(E1 - E0) <= 1e-12 * abs(E0)
