@@ -812,36 +812,14 @@ struct Family {
   // One sweep over all element batches: E-vector of M times the MODE vector.
   // With dot != nullptr each thread also accumulates sum_e u_e . (M_e u_e) over
   // the values it stores: the energy u^T M u of the swept vector, element by element.
-  // Batch bt of an element sweep over gridDim.x blocks (block b takes b, b + G, ...):
-  // full batches of NBC elements for the R = NE / (G NBC) full rounds, then the
-  // remaining elements split as evenly as possible into one batch per block, so the
-  // last round ends within one element per block instead of one batch.
-  static __device__ __forceinline__ int sweep_nbatch(int ne) {
-    const int G = gridDim.x, full = ne / (G * NBC) * G, rem = ne - full * NBC;
-    return full + min(G, rem);
-  }
-  static __device__ __forceinline__ void sweep_batch(int ne, int bt, int &e0, int &nb) {
-    const int G = gridDim.x, full = ne / (G * NBC) * G;
-    if (bt < full) {
-      e0 = bt * NBC;
-      nb = NBC;
-      return;
-    }
-    const int rem = ne - full * NBC, nl = min(G, rem), j = bt - full;
-    const int base = rem / nl, extra = rem - base * nl;
-    e0 = full * NBC + j * base + min(j, extra);
-    nb = base + (j < extra ? 1 : 0);
-  }
-
   template <int MODE, typename T>
   static __device__ __forceinline__ void sweep_matvec(const MeshDesc &m, int *eb, const T *tb, const T *tbt, T *u,
                                                       T *S, T *uq, T *y, const T *mq, const T *idv, const T *x,
                                                       const T *r, const T *q, const T *p, T alpha, T beta,
                                                       T *evec, T *dot = nullptr) {
-    const int nbatch = sweep_nbatch(m.ne);
+    const int nbatch = (m.ne + NBC - 1) / NBC;
     for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
-      int e0, nb;
-      sweep_batch(m.ne, bt, e0, nb);
+      const int e0 = bt * NBC, nb = min(NBC, m.ne - e0);
       if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, e0 + threadIdx.x);
       __syncthreads();
       for (int k = threadIdx.x; k < CXC * ND; k += blockDim.x) {
