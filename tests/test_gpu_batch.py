@@ -142,3 +142,46 @@ def test_configured_256_problem_batch_matches_one_by_one_and_oracle():
     batch.close()
     for c in ctxs:
         c.close()
+
+
+def test_tile_shapes_change_no_result_beyond_the_solver_sums():
+    """The autotuner's axes, set directly. Element batches per work item and threads per
+    block only regroup loops that stride by the block size, so every per-value result,
+    and hence the fields, are bitwise the same. Solver batches per work item regroup the
+    per-problem dot-product partials: the fields then agree to the 1e-12 relative bar of
+    the batched-vs-unbatched comparison. Values outside the lists are rejected."""
+    from paper_2112_07075_b300.lh import Batch
+    probs = _problems()
+    steps, dt = 3, 5e-4
+    shapes = [((1, 1, 1, 1), (1, 1, 1, 1), 128),
+              ((2, 4, 2, 1), (1, 1, 1, 1), 512),
+              ((4, 1, 4, 2), (1, 1, 1, 1), 256),
+              ((4, 2, 1, 2), (4, 2, 1, 4), 256)]
+    out = []
+    for tiles, tiles_cg, threads in shapes:
+        ctxs, states = [], []
+        for pr in probs:
+            ctx, _, _ = _make(pr)
+            ctxs.append(ctx)
+            states.append(ctx.init_state(pr["kind"]))
+        batch = Batch(ctxs, states, [dt] * len(ctxs))
+        batch.set_config(tiles, tiles_cg, threads)
+        for _ in range(steps):
+            batch.step()
+        torch.cuda.synchronize()
+        infos = batch.read_infos()
+        assert all(i.steps == steps and i.status == 0 for i in infos)
+        out.append([[t.cpu().numpy() for t in s] for s in states])
+        if len(out) == 1:
+            with pytest.raises(Exception):
+                batch.set_config((3, 1, 1, 1), (1, 1, 1, 1), 256)
+            with pytest.raises(Exception):
+                batch.set_config((1, 1, 1, 1), (1, 1, 1, 1), 96)
+        batch.close()
+    for k in (1, 2):   # element tiles and threads only: bitwise
+        for a, b in zip(out[0], out[k]):
+            for fa, fb in zip(a, b):
+                assert np.array_equal(fa, fb)
+    for a, b in zip(out[0], out[3]):   # solver tiles too: the dot products' grouping
+        for fa, fb in zip(a, b):
+            assert np.linalg.norm(fa - fb) <= 1e-12 * np.linalg.norm(fb)
