@@ -940,12 +940,14 @@ lh_status lh_batch_autotune(lh_batch *b, int *cfg_out) {
       bool present = false;
       for (int o : b->order) present |= o == p;
       if (!present) continue;
-      for (int t : {2, 4})
-        if ((result = try_cfg(p - 1, t)) != LH_OK) break;
-      for (int t : {2, 4})
+      // every listed value (try_cfg skips the current one), so a search that starts
+      // from a shape set by lh_batch_set_config explores the same candidates
+      for (int t : {1, 2, 4})
+        if (result == LH_OK) result = try_cfg(p - 1, t);
+      for (int t : {1, 2, 4})
         if (result == LH_OK) result = try_cfg(3 + p, t);
     }
-    for (int t : {128, 512})
+    for (int t : {128, 256, 512})
       if (result == LH_OK) result = try_cfg(8, t);
   } while (false);
   const cudaError_t er = copy_all(false);
