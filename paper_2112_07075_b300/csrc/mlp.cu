@@ -67,6 +67,33 @@ struct GemmCfg {
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+// Sixteen consecutive outputs of one row: two 16-byte stores (BF16) or four
+// (FP32) where the address allows, else element by element (the same values).
+__device__ __forceinline__ void st16_f32(float *p, const float (&v)[16]) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+    for (int l = 0; l < 16; l += 4) *reinterpret_cast<float4 *>(p + l) = make_float4(v[l], v[l + 1], v[l + 2], v[l + 3]);
+  } else {
+#pragma unroll
+    for (int l = 0; l < 16; ++l) p[l] = v[l];
+  }
+}
+__device__ __forceinline__ void st16_bf16(__nv_bfloat16 *p, const float (&v)[16]) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    uint32_t w[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * l], v[2 * l + 1]);
+      w[l] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    reinterpret_cast<uint4 *>(p)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4 *>(p)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  } else {
+#pragma unroll
+    for (int l = 0; l < 16; ++l) p[l] = __float2bfloat16(v[l]);
+  }
+}
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
@@ -184,15 +211,24 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
         continue;
       }
       const size_t idx = (size_t)m * g.ldc + n;
+      // each thread owns a row: its 16 outputs are contiguous, so they go out as
+      // whole 16-byte stores (one thread per row makes the element-wise form 16
+      // scattered stores per chunk and output)
+      float z[16], o[16];
 #pragma unroll
       for (int l = 0; l < 16; ++l) {
-        float z = v[l];
-        if (g.bias) z += g.bias[n + l];
-        if (g.pre) g.pre[idx + l] = z;
-        const float o = g.gelu ? gelu_f(z) : z;
-        if (g.C32) g.C32[idx + l] = g.accumulate ? g.C32[idx + l] + o : o;
-        if (g.C16) g.C16[idx + l] = __float2bfloat16(o);
+        z[l] = g.bias ? v[l] + g.bias[n + l] : v[l];
+        o[l] = g.gelu ? gelu_f(z[l]) : z[l];
       }
+      if (g.pre) st16_f32(g.pre + idx, z);
+      if (g.C32) {
+        if (g.accumulate) {
+#pragma unroll
+          for (int l = 0; l < 16; ++l) o[l] = g.C32[idx + l] + o[l];
+        }
+        st16_f32(g.C32 + idx, o);
+      }
+      if (g.C16) st16_bf16(g.C16 + idx, o);
     }
   }
   tc::fence_before_sync();
@@ -409,16 +445,17 @@ lh_status mfail(lh_mlp *m, lh_status s, const std::string &msg) {
   return s;
 }
 
-// forward pass for n rows already packed in m->Xh; Y (FP32) out
-bool forward(lh_mlp *m, int n, float *Y, cudaStream_t s) {
+// forward pass for n rows already packed in m->Xh; Y (FP32) out. keep_pre: also
+// store the layers' pre-activations (needed by the backward pass only)
+bool forward(lh_mlp *m, int n, float *Y, cudaStream_t s, bool keep_pre) {
   bool ok = true;
   GemmArgs g{};
   g.A = m->Xh; g.B = m->wh + oW1; g.M = n; g.N = kHid; g.K = kInPad; g.lda = kInPad; g.ldb = kInPad;
-  g.bias = m->w + oB1; g.C16 = m->H1h; g.pre = m->Z1; g.ldc = kHid; g.gelu = 1; g.status = m->status;
+  g.bias = m->w + oB1; g.C16 = m->H1h; g.pre = keep_pre ? m->Z1 : nullptr; g.ldc = kHid; g.gelu = 1; g.status = m->status;
   ok = ok && gemm<A_ROW, B_NMAJOR, kHid>(g, s);
   g = GemmArgs{};
   g.A = m->H1h; g.B = m->wh + oW2; g.M = n; g.N = kHid; g.K = kHid; g.lda = kHid; g.ldb = kHid;
-  g.bias = m->w + oB2; g.C16 = m->H2h; g.pre = m->Z2; g.ldc = kHid; g.gelu = 1; g.status = m->status;
+  g.bias = m->w + oB2; g.C16 = m->H2h; g.pre = keep_pre ? m->Z2 : nullptr; g.ldc = kHid; g.gelu = 1; g.status = m->status;
   ok = ok && gemm<A_ROW, B_NMAJOR, kHid>(g, s);
   g = GemmArgs{};
   g.A = m->H2h; g.B = m->wh + oW3; g.M = n; g.N = kOut; g.K = kHid; g.lda = kHid; g.ldb = kHid;
@@ -564,7 +601,7 @@ lh_status lh_mlp_forward(lh_mlp *m, const float *X, int n, float *Y, lh_stream_t
   if (n > m->max_rows) return mfail(m, LH_ERR_ARG, "more rows than the MLP was created for");
   cudaStream_t s = (cudaStream_t)stream;
   k_pack_input<<<1024, 256, 0, s>>>(n, X, m->Xh);
-  if (!forward(m, n, Y, s)) return mfail(m, LH_ERR_CUDA, "MLP forward: tensor map or launch failed");
+  if (!forward(m, n, Y, s, false)) return mfail(m, LH_ERR_CUDA, "MLP forward: tensor map or launch failed");
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LH_OK : mfail(m, LH_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -575,7 +612,7 @@ lh_status lh_mlp_gradients(lh_mlp *m, const float *X, const float *T, int n, flo
   if (n > m->max_rows) return mfail(m, LH_ERR_ARG, "more rows than the MLP was created for");
   cudaStream_t s = (cudaStream_t)stream;
   k_pack_input<<<1024, 256, 0, s>>>(n, X, m->Xh);
-  if (!forward(m, n, m->Y, s) || !backward(m, n, T, loss, s))
+  if (!forward(m, n, m->Y, s, true) || !backward(m, n, T, loss, s))
     return mfail(m, LH_ERR_CUDA, "MLP gradients: tensor map or launch failed");
   if (grads) cudaMemcpyAsync(grads, m->g, kNParam * 4, cudaMemcpyDeviceToDevice, s);
   const cudaError_t e = cudaGetLastError();
