@@ -34,7 +34,10 @@
 using namespace lh;
 using namespace lh::mlp;
 
-extern "C" lh_status lh_mlp_forward(lh_mlp *m, const float *X, int n, float *Y, lh_stream_t stream);
+namespace lh {
+__nv_bfloat16 *mlp_packed_input(lh_mlp *m, int *max_rows);
+lh_status mlp_forward_packed(lh_mlp *m, int n, float *Y, cudaStream_t s);
+}  // namespace lh
 
 namespace lh {
 namespace learn {
@@ -81,31 +84,39 @@ __global__ void k_scale_final(int nb, const double *__restrict__ part, double *_
 // X[e][384 + c*64 + i] = (a_2 - a_3) / s_d at node(e, i), component c.
 // Row r of X holds element e = off + r * stride (stride 1, off 0: every element).
 // One thread per (row, element node): the node's index is formed once and its three
-// components of the three history vectors give nine features.
+// components of the three history vectors give nine features. OT = float: rows of
+// kIn floats (recorded training data); OT = BF16: straight into the network's packed
+// input, rows of ldx values (the value is the float feature rounded to nearest, the
+// same as packing the float rows).
+__device__ __forceinline__ void put_feature(float *p, float v) { *p = v; }
+__device__ __forceinline__ void put_feature(__nv_bfloat16 *p, float v) { *p = __float2bfloat16(v); }
+
+template <typename OT>
 __global__ void k_hist_features(MeshDesc m, int rows, int stride, int off, const double *__restrict__ h0,
                                 const double *__restrict__ h1, const double *__restrict__ h2,
-                                const double *__restrict__ s, float *__restrict__ X) {
+                                const double *__restrict__ s, OT *__restrict__ X, int ldx) {
   const size_t total = (size_t)rows * ND;
   const double is = 1.0 / s[0], isd = 1.0 / s[1];
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / ND), i = (int)(t % ND);
     const int e = off + r * stride;
     const size_t g = (size_t)h1_base<3, D>(m, e) + h1_local<3, D>(m, i);
-    float *xr = X + (size_t)r * kIn;
+    OT *xr = X + (size_t)r * ldx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t gi = (size_t)c * m.nh1 + g;
       const double a0 = h0[gi], a1 = h1[gi], a2 = h2[gi];
-      xr[c * ND + i] = (float)(a0 * is);
-      xr[192 + c * ND + i] = (float)((a0 - a1) * isd);
-      xr[384 + c * ND + i] = (float)((a1 - a2) * isd);
+      put_feature(xr + c * ND + i, (float)(a0 * is));
+      put_feature(xr + 192 + c * ND + i, (float)((a0 - a1) * isd));
+      put_feature(xr + 384 + c * ND + i, (float)((a1 - a2) * isd));
     }
   }
 }
 
 // Jacobian features at the element centroid: 9 entries of J / (h0 p) and det J / (h0 p)^3.
+template <typename OT>
 __global__ void k_jac_features(MeshDesc m, int rows, int stride, int off, const double *__restrict__ x, Cent cb,
-                               double hs, float *__restrict__ X) {
+                               double hs, OT *__restrict__ X, int ldx) {
   // FP32 arithmetic (the features feed a BF16 network); positions are taken relative
   // to the element's first node, which leaves J unchanged (the basis derivatives sum
   // to zero) and avoids cancellation between O(1) coordinates
@@ -139,9 +150,9 @@ __global__ void k_jac_features(MeshDesc m, int rows, int stride, int off, const 
     }
     const float det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
                       J[2] * (J[3] * J[7] - J[4] * J[6]);
-    float *out = X + (size_t)r * kIn + 576;
-    for (int k = 0; k < 9; ++k) out[k] = J[k];
-    out[9] = det;
+    OT *out = X + (size_t)r * ldx + 576;
+    for (int k = 0; k < 9; ++k) put_feature(out + k, J[k]);
+    put_feature(out + 9, det);
   }
 }
 
@@ -273,7 +284,7 @@ struct lh_learn {
   char *arena = nullptr;
   double *hist[3] = {nullptr, nullptr, nullptr};
   int count = 0, head = 0;   // solutions stored, next ring slot
-  float *X = nullptr, *Y = nullptr, *evA32 = nullptr;
+  float *Y = nullptr, *evA32 = nullptr;
   double *bprev = nullptr;   // right-hand side of the previous solve
   int stride = 1;            // recording: every stride-th element of a solve
   float *mq32 = nullptr;     // FP32 mass data for the residual check (own copy for FP64 contexts)
@@ -304,7 +315,7 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
   const double *a1 = hist_at(L, 0);
   k_sumsq<<<kBlocks, 256, 0, s>>>(nv, a1, hist_at(L, 1), c->invdiag, L->part);
   k_scale_final<<<1, 32, 0, s>>>(kBlocks, L->part, L->scale);
-  float *X = L->X;
+  float *X = nullptr;   // recording: this solve's rows of the caller's buffer
   L->pending = false;
   int rows = m.ne, stride = 1, off = 0;
   if (L->mode == 1) {
@@ -317,10 +328,24 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
     L->pend_rows = rows;
     L->pend_off = off;
   }
-  k_hist_features<<<4 * kBlocks, 256, 0, s>>>(m, rows, stride, off, a1, hist_at(L, 1), hist_at(L, 2), L->scale, X);
-  k_jac_features<<<(rows + 255) / 256, 256, 0, s>>>(m, rows, stride, off, x, L->cent, L->hs, X);
+  if (L->mode == 1) {
+    k_hist_features<<<4 * kBlocks, 256, 0, s>>>(m, rows, stride, off, a1, hist_at(L, 1), hist_at(L, 2), L->scale,
+                                                X, kIn);
+    k_jac_features<<<(rows + 255) / 256, 256, 0, s>>>(m, rows, stride, off, x, L->cent, L->hs, X, kIn);
+  } else {
+    // prediction: the features go straight into the network's packed BF16 input
+    int cap = 0;
+    __nv_bfloat16 *Xh = mlp_packed_input(L->mlp, &cap);
+    if (!Xh || m.ne > cap) {
+      c->err = "learned guess: the MLP was created for fewer rows than the mesh has elements";
+      return LH_ERR_ARG;
+    }
+    k_hist_features<<<4 * kBlocks, 256, 0, s>>>(m, rows, stride, off, a1, hist_at(L, 1), hist_at(L, 2), L->scale,
+                                                Xh, kInPad);
+    k_jac_features<<<(rows + 255) / 256, 256, 0, s>>>(m, rows, stride, off, x, L->cent, L->hs, Xh, kInPad);
+  }
   if (L->mode == 2) {
-    if (lh_status st = lh_mlp_forward(L->mlp, X, m.ne, L->Y, (lh_stream_t)s)) return st;
+    if (lh_status st = mlp_forward_packed(L->mlp, m.ne, L->Y, s)) return st;
     k_assemble<<<2 * kBlocks, 256, 0, s>>>(m, L->Y, a1, L->scale, c->invdiag, L->guess);
     k_resid_elem<<<(m.ne + kResidNb - 1) / kResidNb, kResidThreads, L->smem_resid, s>>>(m, c->tab, L->mq32,
                                                                                          L->guess, c->invdiag,
@@ -403,7 +428,7 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   const size_t nv = c->nv, ne = c->mesh.ne;
   const bool own_mq32 = c->mq32 == nullptr;
   const size_t nq = ne * (size_t)c->nq;
-  const size_t bytes_list[] = {3 * nv * 8, ne * lh::mlp::kIn * 4, ne * lh::mlp::kOut * 4, ne * 3 * 64 * 4,
+  const size_t bytes_list[] = {3 * nv * 8, 0, ne * lh::mlp::kOut * 4, ne * 3 * 64 * 4,
                                nv * 8, nv * 8, 4 * 1184 * 8 + 1024, own_mq32 ? nq * 4 : 0};
   size_t bytes = 0;
   for (size_t b : bytes_list) bytes += (b + 255) / 256 * 256;
@@ -417,7 +442,6 @@ lh_status lh_learn_attach(lh_ctx *c, lh_mlp *mlp, int mode, float *X_buf, float 
   auto take = [&](size_t b) { char *q = p; p += (b + 255) / 256 * 256; return q; };
   double *h = (double *)take(bytes_list[0]);
   for (int k = 0; k < 3; ++k) L->hist[k] = h + k * nv;
-  L->X = (float *)take(bytes_list[1]);
   L->Y = (float *)take(bytes_list[2]);
   L->evA32 = (float *)take(bytes_list[3]);
   L->bprev = (double *)take(bytes_list[4]);

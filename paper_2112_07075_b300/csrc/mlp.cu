@@ -634,3 +634,20 @@ lh_status lh_mlp_train_step(lh_mlp *m, const float *X, const float *T, int n, fl
 }
 
 }  // extern "C"
+
+namespace lh {
+// For the learned form, which writes its features straight into the network's
+// packed BF16 input ([max_rows][kInPad], padding columns zero since creation and
+// never written): the buffer and its row capacity, and the forward pass from it.
+__nv_bfloat16 *mlp_packed_input(lh_mlp *m, int *max_rows) {
+  if (max_rows) *max_rows = m ? m->max_rows : 0;
+  return m ? m->Xh : nullptr;
+}
+lh_status mlp_forward_packed(lh_mlp *m, int n, float *Y, cudaStream_t s) {
+  if (!m || !Y || n < 1) return mfail(m, LH_ERR_ARG, "bad MLP forward arguments");
+  if (n > m->max_rows) return mfail(m, LH_ERR_ARG, "more rows than the MLP was created for");
+  if (!forward(m, n, Y, s, false)) return mfail(m, LH_ERR_CUDA, "MLP forward: tensor map or launch failed");
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LH_OK : mfail(m, LH_ERR_CUDA, cudaGetErrorString(e));
+}
+}  // namespace lh
