@@ -37,7 +37,7 @@ namespace {
 // Epilogue: C32 (FP32) and/or C16 (BF16) with optional bias and GELU; when PRE
 // is given the pre-activation is written there (FP32).
 // ---------------------------------------------------------------------------
-constexpr int kStages = 4;
+constexpr int kStages = 2;
 constexpr int kBK = 64;   // K per stage: one 128-byte swizzle row of BF16
 constexpr long long kSpin = 2000000000LL;   // bounded waits (~1 s)
 
