@@ -96,7 +96,10 @@ __global__ void k_hist_features(MeshDesc m, int rows, int stride, int off, const
                                 const double *__restrict__ h1, const double *__restrict__ h2,
                                 const double *__restrict__ s, OT *__restrict__ X, int ldx) {
   const size_t total = (size_t)rows * ND;
-  const double is = 1.0 / s[0], isd = 1.0 / s[1];
+  // the differences are formed in FP64 (consecutive solutions can agree to many
+  // digits), the scalings in FP32: the features feed a BF16 network, and FP64
+  // multiplies run at 1/64 of the FP32 rate on this part
+  const float is = (float)(1.0 / s[0]), isd = (float)(1.0 / s[1]);
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / ND), i = (int)(t % ND);
     const int e = off + r * stride;
@@ -106,9 +109,9 @@ __global__ void k_hist_features(MeshDesc m, int rows, int stride, int off, const
     for (int c = 0; c < 3; ++c) {
       const size_t gi = (size_t)c * m.nh1 + g;
       const double a0 = h0[gi], a1 = h1[gi], a2 = h2[gi];
-      put_feature(xr + c * ND + i, (float)(a0 * is));
-      put_feature(xr + 192 + c * ND + i, (float)((a0 - a1) * isd));
-      put_feature(xr + 384 + c * ND + i, (float)((a1 - a2) * isd));
+      put_feature(xr + c * ND + i, (float)a0 * is);
+      put_feature(xr + 192 + c * ND + i, (float)(a0 - a1) * isd);
+      put_feature(xr + 384 + c * ND + i, (float)(a1 - a2) * isd);
     }
   }
 }
@@ -177,11 +180,14 @@ __global__ void k_assemble(MeshDesc m, const float *__restrict__ Y, const double
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < m.nh1; n += gridDim.x * blockDim.x) {
     int off[8];
     const int cnt = node_copies<3, D>(m, n, 3, off);
+    // cnt = 1, 2, 4 or 8 (one or two owners per axis): dividing by it is the exact
+    // scaling by 2^-log2(cnt), done here without an FP64 division
+    const double icnt = __hiloint2double((1023 - (__ffs(cnt) - 1)) << 20, 0);
     for (int c = 0; c < 3; ++c) {
       const size_t k = (size_t)c * m.nh1 + n;
       double sum = 0.0;
       for (int j = 0; j < cnt; ++j) sum += (double)Y[off[j] + c * ND];
-      g[k] = idg[k] != 0.0 ? fma(sc, sum / cnt, a1[k]) : 0.0;
+      g[k] = idg[k] != 0.0 ? fma(sc, sum * icnt, a1[k]) : 0.0;
     }
   }
 }
