@@ -200,8 +200,7 @@ constexpr int kResidS = interp_scratch<3, D, 6>(kResidCx) > interp_scratch<3, 6,
 constexpr size_t kResidSmem = sizeof(float) * (2 * 6 * D + kResidCx * ND + kResidS + kResidCx * 216 + kResidCx * ND);
 __global__ void __launch_bounds__(kResidThreads) k_resid_elem(MeshDesc m, const double *__restrict__ tab,
                                                               const float *__restrict__ mq32,
-                                                              const double *__restrict__ g,
-                                                              const double *__restrict__ idg, float *__restrict__ evA) {
+                                                              const double *__restrict__ g, float *__restrict__ evA) {
   constexpr int CX = kResidCx, NQ = 216, Q = 6;
   extern __shared__ double smd[];
   float *tb = (float *)smd, *tbt = tb + Q * D, *u = tbt + Q * D, *S = u + CX * ND, *uq = S + kResidS, *y = uq + CX * NQ;
@@ -212,18 +211,18 @@ __global__ void __launch_bounds__(kResidThreads) k_resid_elem(MeshDesc m, const 
     float val = 0.0f;
     if (b < nb) {
       const size_t gi = (size_t)c * m.nh1 + h1_base<3, D>(m, e0 + b) + h1_local<3, D>(m, i);
-      val = idg[gi] != 0.0 ? (float)g[gi] : 0.0f;
+      val = (float)g[gi];   // k_assemble leaves g = 0 on the constrained DOFs
     }
     u[k] = val;
   }
   __syncthreads();
-  interp<3, D, Q, CX>(u, uq, S, tb);
+  interp_p<3, D, Q, CX>(u, uq, S, tb);   // pencil form: FP32 work is cheap, smem traffic is not
   for (int k = threadIdx.x; k < CX * NQ; k += blockDim.x) {
     const int q = k % NQ, b = (k / NQ) / 3;
     uq[k] *= b < nb ? mq32[(size_t)(e0 + b) * NQ + q] : 0.0f;
   }
   __syncthreads();
-  interp<3, Q, D, CX>(uq, y, S, tbt);
+  interp_p<3, Q, D, CX>(uq, y, S, tbt);
   for (int k = threadIdx.x; k < nb * 3 * ND; k += blockDim.x) evA[(size_t)e0 * 3 * ND + k] = y[k];
 }
 
@@ -354,8 +353,7 @@ lh_status learn_before_solve(lh_ctx *c, const double *x, cudaStream_t s) {
     if (lh_status st = mlp_forward_packed(L->mlp, m.ne, L->Y, s)) return st;
     k_assemble<<<2 * kBlocks, 256, 0, s>>>(m, L->Y, a1, L->scale, c->invdiag, L->guess);
     k_resid_elem<<<(m.ne + kResidNb - 1) / kResidNb, kResidThreads, L->smem_resid, s>>>(m, c->tab, L->mq32,
-                                                                                         L->guess, c->invdiag,
-                                                                                         L->evA32);
+                                                                                         L->guess, L->evA32);
     k_resid_nodes<<<kBlocks, 256, 0, s>>>(m, c->rhs, L->bprev, c->invdiag, L->evA32, L->part);
     k_decide<<<1, 32, 0, s>>>(kBlocks, L->part, L->flag, L->used, L->ratio);
     k_apply<<<kBlocks, 256, 0, s>>>(nv, L->flag, L->guess, c->a_prev);
