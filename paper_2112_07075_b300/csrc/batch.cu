@@ -196,6 +196,8 @@ __device__ __forceinline__ double b_cg_matvec(const BProb &pb, int e0, int mode,
   __shared__ int s_eb[F2<1>::NBC];
   const MeshDesc &m = pb.m;
   const int nb = min(F::NBC, m.ne - e0);
+  double mqr[F::MQT_C];   // mass data first: the loads overlap the gather below
+  F::template load_mq<double>(pb.mq, e0, nb, mqr);
   for (int k = threadIdx.x; k < F::oZ + F::D; k += blockDim.x) st[k] = pb.tab[k];
   if (threadIdx.x < nb) s_eb[threadIdx.x] = h1_base<2, F::D>(m, e0 + threadIdx.x);
   __syncthreads();
@@ -210,7 +212,7 @@ __device__ __forceinline__ double b_cg_matvec(const BProb &pb, int e0, int mode,
     u[k] = val;
   }
   __syncthreads();
-  F::template batch_matvec<double>(st + F::oB, st + F::oBt, u, S, uq, y, pb.mq, e0, nb);
+  F::template batch_matvec_r<double>(st + F::oB, st + F::oBt, u, S, uq, y, mqr);
   double d = 0.0;
   for (int k = threadIdx.x; k < nb * 2 * ND; k += blockDim.x) {
     const double yk = y[k];

@@ -795,6 +795,33 @@ struct Family {
     interp<DIM, Q, D, CXC>(uq, y, S, tbt);
   }
 
+  // The same product with the batch's mass data loaded into registers by the caller
+  // (load_mq) before its gather: where the data come from DRAM (the batched solver,
+  // whose problems do not fit L2 together), those loads overlap the gather and the
+  // first contraction instead of following them. Needs blockDim.x == TC.
+  static constexpr int MQT_C = (CXC * NQ + TC - 1) / TC;
+  template <typename T>
+  static __device__ __forceinline__ void load_mq(const T *__restrict__ mq, int e0, int nb, T (&r)[MQT_C]) {
+#pragma unroll
+    for (int j = 0; j < MQT_C; ++j) {
+      const int k = threadIdx.x + j * TC;
+      const int q = k % NQ, b = (k / NQ) / DIM;
+      r[j] = (k < CXC * NQ && b < nb) ? mq[(size_t)(e0 + b) * NQ + q] : (T)0;
+    }
+  }
+  template <typename T>
+  static __device__ __forceinline__ void batch_matvec_r(const T *tb, const T *tbt, const T *u, T *S, T *uq, T *y,
+                                                        const T (&r)[MQT_C]) {
+    interp<DIM, D, Q, CXC>(u, uq, S, tb);
+#pragma unroll
+    for (int j = 0; j < MQT_C; ++j) {
+      const int k = threadIdx.x + j * TC;
+      if (k < CXC * NQ) uq[k] *= r[j];
+    }
+    __syncthreads();
+    interp<DIM, Q, D, CXC>(uq, y, S, tbt);
+  }
+
   // Search-direction value at a node: p_new = invdiag*(r - alpha q) + beta p (MODE 2),
   // p0 = invdiag*r (MODE 1), invdiag*r + beta p (MODE 3), z + beta p with z = invdiag*r
   // passed as x (MODE 4), or the masked vector x (MODE 0).
