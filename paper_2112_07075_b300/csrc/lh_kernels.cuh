@@ -847,6 +847,8 @@ struct Family {
     const int nbatch = (m.ne + NBC - 1) / NBC;
     for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
       const int e0 = bt * NBC, nb = min(NBC, m.ne - e0);
+      T mqr[MQT_C];   // mass data first: the loads overlap the gather below
+      load_mq<T>(mq, e0, nb, mqr);
       if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, e0 + threadIdx.x);
       __syncthreads();
       for (int k = threadIdx.x; k < CXC * ND; k += blockDim.x) {
@@ -856,7 +858,7 @@ struct Family {
         u[k] = val;
       }
       __syncthreads();
-      batch_matvec<T>(tb, tbt, u, S, uq, y, mq, e0, nb);
+      batch_matvec_r<T>(tb, tbt, u, S, uq, y, mqr);
       if (dot) {
         T d = *dot;
         for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) {
