@@ -796,15 +796,17 @@ struct Family {
   }
 
   // The same product with the batch's mass data loaded into registers by the caller
-  // (load_mq) before its gather: where the data come from DRAM (the batched solver,
-  // whose problems do not fit L2 together), those loads overlap the gather and the
-  // first contraction instead of following them. Needs blockDim.x == TC.
+  // (load_mq) before its gather, so that those loads overlap the gather and the
+  // first contraction instead of following them. Value k of the batch belongs to
+  // thread k mod blockDim.x; MQT_C values per thread cover the batch only when
+  // blockDim.x >= TC, which the callers check (the tensor-core solver runs this
+  // family's FP64 sweeps with a different block size).
   static constexpr int MQT_C = (CXC * NQ + TC - 1) / TC;
   template <typename T>
   static __device__ __forceinline__ void load_mq(const T *__restrict__ mq, int e0, int nb, T (&r)[MQT_C]) {
 #pragma unroll
     for (int j = 0; j < MQT_C; ++j) {
-      const int k = threadIdx.x + j * TC;
+      const int k = threadIdx.x + j * blockDim.x;
       const int q = k % NQ, b = (k / NQ) / DIM;
       r[j] = (k < CXC * NQ && b < nb) ? mq[(size_t)(e0 + b) * NQ + q] : (T)0;
     }
@@ -815,7 +817,7 @@ struct Family {
     interp<DIM, D, Q, CXC>(u, uq, S, tb);
 #pragma unroll
     for (int j = 0; j < MQT_C; ++j) {
-      const int k = threadIdx.x + j * TC;
+      const int k = threadIdx.x + j * blockDim.x;
       if (k < CXC * NQ) uq[k] *= r[j];
     }
     __syncthreads();
@@ -847,8 +849,9 @@ struct Family {
     const int nbatch = (m.ne + NBC - 1) / NBC;
     for (int bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
       const int e0 = bt * NBC, nb = min(NBC, m.ne - e0);
+      const bool pre = blockDim.x >= TC;   // block-uniform
       T mqr[MQT_C];   // mass data first: the loads overlap the gather below
-      load_mq<T>(mq, e0, nb, mqr);
+      if (pre) load_mq<T>(mq, e0, nb, mqr);
       if (threadIdx.x < nb) eb[threadIdx.x] = h1_base<DIM, D>(m, e0 + threadIdx.x);
       __syncthreads();
       for (int k = threadIdx.x; k < CXC * ND; k += blockDim.x) {
@@ -858,7 +861,8 @@ struct Family {
         u[k] = val;
       }
       __syncthreads();
-      batch_matvec_r<T>(tb, tbt, u, S, uq, y, mqr);
+      if (pre) batch_matvec_r<T>(tb, tbt, u, S, uq, y, mqr);
+      else batch_matvec<T>(tb, tbt, u, S, uq, y, mq, e0, nb);
       if (dot) {
         T d = *dot;
         for (int k = threadIdx.x; k < nb * DIM * ND; k += blockDim.x) {
