@@ -382,21 +382,34 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
         for (int g = w.g0 + threadIdx.x; g < w.g1; g += blockDim.x) {
           int off[4];
           const int n = table_copies(pb.ncopy, g, off);
+          // every load of both components first (the problems live in DRAM), then
+          // the arithmetic in the same order as one component at a time
+          double idg[2], rv[2], pv[2], av[2], ev[2][4];
+#pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int k = c * pb.m.nh1 + g;
-            const double idg = pb.invdiag[k];
-            if (idg != 0.0) {
-              double qv = pb.evec[off[0] + c * ND];
-              for (int j = 1; j < n; ++j) qv += pb.evec[off[j] + c * ND];
-              const double rv = pb.r[k];
-              const double pn = fma(beta, pb.p[k], idg * rv);
-              const double r2 = fma(-alpha, qv, rv);
-              pb.p[k] = pn;
-              pb.a[k] = fma(alpha, pn, pb.a[k]);
-              pb.r[k] = r2;
-              acc[0] = fma(r2, r2, acc[0]);
-              acc[1] = fma(r2 * idg, r2, acc[1]);
-            }
+            idg[c] = pb.invdiag[k];
+            rv[c] = pb.r[k];
+            pv[c] = pb.p[k];
+            av[c] = pb.a[k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ev[c][j] = j < n ? pb.evec[off[j] + c * ND] : 0.0;
+          }
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (idg[c] == 0.0) continue;
+            const int k = c * pb.m.nh1 + g;
+            double qv = ev[c][0];
+#pragma unroll
+            for (int j = 1; j < 4; ++j)
+              if (j < n) qv += ev[c][j];
+            const double pn = fma(beta, pv[c], idg[c] * rv[c]);
+            const double r2 = fma(-alpha, qv, rv[c]);
+            pb.p[k] = pn;
+            pb.a[k] = fma(alpha, pn, av[c]);
+            pb.r[k] = r2;
+            acc[0] = fma(r2, r2, acc[0]);
+            acc[1] = fma(r2 * idg[c], r2, acc[1]);
           }
         }
       });
