@@ -337,8 +337,7 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
     const int nact = *(volatile int *)A.active;
     if (nact == 0 || iter >= A.max_it) break;
     // E: element matvec of p_new = invdiag r + beta p for active problems, with
-    // p_new . M p_new summed element by element; the last item of a problem sums the
-    // item partials in item order and forms alpha
+    // p_new . M p_new summed element by element into one partial per item
     for (int it = blockIdx.x; it < A.nitems_e; it += G) {
       const ItemE w = A.items_e[it];
       BScal &sc = A.scal[w.pid];
@@ -352,30 +351,28 @@ __global__ void __launch_bounds__(kThreadsCG) k_b_cg(BCgArgs A) {
       });
       block_sum<1>(acc, red);
       if (threadIdx.x == 0) A.partials_e[it] = acc[0];
-      if (last_item(sc, pb.n_eitems)) {
-        if (threadIdx.x < 32) {
-          __threadfence();
-          double t = 0.0;
-          for (int i = threadIdx.x; i < pb.n_eitems; i += 32)
-            t += ((volatile const double *)A.partials_e)[pb.first_eitem + i];
-          t = warp_sum(t);
-          if (threadIdx.x == 0) {
-            sc.cnt = 0;
-            sc.alpha = sc.rz / t;
-          }
-        }
-        __syncthreads();
-      }
     }
     if (!sync()) return;
     // B: one node sweep: q = M p_new gathered, p = p_new, a += alpha p, r -= alpha q,
-    // r.r and r.z; the last item of a problem forms beta and tests convergence
+    // r.r and r.z; the last item of a problem forms beta and tests convergence.
+    // alpha = r.z / p.Mp is formed by every node item of the problem from the element
+    // items' partials, summed in item order (the same value in every block): there are
+    // a few node items per block and many element items, so this costs less than an
+    // atomic-counted last element item per problem
     for (int it = blockIdx.x; it < A.nitems_n; it += G) {
       const ItemN w = A.items_n[it];
       BScal &sc = A.scal[w.pid];
       if (!sc.active) continue;
       const BProb &pb = A.probs[w.pid];
-      const double alpha = sc.alpha, beta = sc.beta;
+      if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < pb.n_eitems; i += 32)
+          t += ((volatile const double *)A.partials_e)[pb.first_eitem + i];
+        t = warp_sum(t);
+        if (threadIdx.x == 0) s_v[2] = sc.rz / t;
+      }
+      __syncthreads();
+      const double alpha = s_v[2], beta = sc.beta;
       double acc[3] = {0.0, 0.0, 0.0};
       dispatch_order(pb.order, [&](auto P) {
         constexpr int D = decltype(P)::value + 1, ND = D * D;
