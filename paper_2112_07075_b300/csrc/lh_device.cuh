@@ -284,6 +284,18 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 __device__ __forceinline__ double warp_sum_partials(const double *p, int n) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
+  if (n <= 10 * 32) {
+    // the usual grid sizes (two CTAs per SM: 296 partials): every load of the lane
+    // is issued before the first add, so the sum costs one memory round trip instead
+    // of one per load after the first eight; the adds run in the same index order
+    double v[10];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) v[j] = lane + 32 * j < n ? p[lane + 32 * j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 10; ++j)
+      if (lane + 32 * j < n) s += v[j];
+    return warp_sum(s);
+  }
   int i = lane;
   for (; i + 7 * 32 < n; i += 8 * 32) {
     double v[8];
@@ -310,6 +322,17 @@ __device__ __forceinline__ void block_chunk(int n, int &k0, int &k1) {
 __device__ __forceinline__ float warp_sum_partials_f(const float *p, int n) {
   const int lane = threadIdx.x & 31;
   float s = 0.0f;
+  if (n <= 10 * 32) {   // one round trip, as in warp_sum_partials
+    float v[10];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) v[j] = lane + 32 * j < n ? p[lane + 32 * j] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 10; ++j)
+      if (lane + 32 * j < n) s += v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+  }
   int i = lane;
   for (; i + 7 * 32 < n; i += 8 * 32) {
     float v[8];
