@@ -47,8 +47,8 @@ WORKLOADS = {
 # capture of the current kernel (profiles/k_cg_tg3d24_q2_fp64.md,
 # profiles/k_cg_ir_tg3d24_q2_fp32ir.md, profiles/k_cg_ir_tg3d32_q4_fp32ir.md); None
 # where no capture of the current kernel exists.
-TRAFFIC = {("tg3d_24_q2", "fp64"): 23387136, ("tg3d_24_q2", "fp32_ir"): 29238016,
-           ("tg3d_32_q4_jit", "fp32_ir"): 10099017728}
+TRAFFIC = {("tg3d_24_q2", "fp64"): 23394816, ("tg3d_24_q2", "fp32_ir"): 29678592,
+           ("tg3d_32_q4_jit", "fp32_ir"): 10096740352}
 METRIC = "MDOF/s of PA force+mass path (RK2-average step, H1 vector DOFs per second)"
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
